@@ -1,0 +1,432 @@
+/*
+ * eamc_oracle.c -- plain, slow, obviously-correct CPU oracle for generalized-ensemble
+ * Monte Carlo on the bimodal (+-J) Edwards-Anderson spin glass.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference legs may load this library.  It shares no code, header,
+ * table or constant generator with the CUDA library: it is written from the paper
+ * (Mueller, Schnabel, Janke, "Nonflat Histogram Techniques for Spin Glasses") and
+ * from the published Philox definition (Salmon, Moraes, Dror, Shaw, SC'11).
+ *
+ * Spins and couplings are stored as int8 values +1/-1 and every energy change is
+ * obtained from the Hamiltonian's definition (Sec. II, Eq. "hamiltonian"):
+ *     H = - sum_<ij> J_ij S_i S_j ,
+ * on an L^dim simple (hyper)cubic lattice with periodic boundaries.
+ *
+ * Conventions fixed where the paper is silent (the same readings are implemented,
+ * independently, by the CUDA path):
+ *   site index   i = x + L*y (+ L*L*z); bond (i,d) joins i and i + e_d (periodic);
+ *                J is stored as J[i*dim + d].
+ *   energy bins  u = number of unsatisfied bonds, E = 2u - dim*V; u's parity never
+ *                changes under single flips, so the bin is b = u >> 1.  E_top is the
+ *                largest attainable E <= 0, b_top its bin (hard wall above it).
+ *   RNG          Philox4x32-10, key = (seed lo, seed hi).  Counter words:
+ *                  disorder      (j>>2, 0, rid, 3)            word j&3, j = bond index
+ *                  initial spins (i>>2, 0, rid, 2 | stream<<8) word i&3
+ *                  MUCA update   (i>>2, t, rid, 0 | stream<<8) word i&3
+ *                  PT update     (8*i + m/4, t, rid>>5, 4 | slot<<8) word m&3,
+ *                                32 words whose bit (rid&31) gives bit 31-m of r
+ *                  PT swap       (k, t, rid, 1) word 0
+ *                A value is "negative" (J=-1, S=-1) iff the word's top bit is set.
+ *   acceptance   thr = 0xFFFFFFFF means "always"; otherwise accept iff r < thr
+ *                (Eq. "muca": P_acc = min(1, W(E_new)/W(E_old)), quantised to 2^-32).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_ALWAYS 0xFFFFFFFFu
+
+/* ---------------------------------------------------------------- Philox4x32-10 */
+/* Salmon et al. (SC'11), Sec. 4.2: the Philox-4x32 S-box multiplies counter words 0
+ * and 2 by two odd constants; the high halves are xored with the other counter words
+ * and the round key, and the key is bumped by the Weyl constants between rounds. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t rand_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                          uint32_t c3, int which) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    return out[which];
+}
+
+/* ---------------------------------------------------------------- lattice basics */
+int or_volume(int dim, int L) { return dim == 2 ? L * L : L * L * L; }
+int or_nbonds(int dim, int L) { return dim * or_volume(dim, L); }
+
+/* neighbour of site i one step along direction d (0=x,1=y,2=z), sign +1 or -1 */
+static int neighbour(int dim, int L, int i, int d, int sign) {
+    int x = i % L, y = (i / L) % L, z = (dim == 3) ? i / (L * L) : 0;
+    int c[3] = {x, y, z};
+    c[d] = (c[d] + sign + L) % L;
+    return c[0] + L * c[1] + L * L * c[2];
+}
+
+/* Quenched disorder (Sec. II): 3V couplings, +1 or -1 with probability 1/2 each. */
+void or_make_disorder(int dim, int L, uint64_t seed, uint32_t rid, int8_t *J) {
+    int nb = or_nbonds(dim, L);
+    for (int j = 0; j < nb; ++j) {
+        uint32_t w = rand_word(seed, (uint32_t)(j >> 2), 0u, rid, 3u, j & 3);
+        J[j] = (w >> 31) ? -1 : +1;
+    }
+}
+
+void or_make_spins(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream, int8_t *S) {
+    int V = or_volume(dim, L);
+    for (int i = 0; i < V; ++i) {
+        uint32_t w = rand_word(seed, (uint32_t)(i >> 2), 0u, rid, 2u | (stream << 8), i & 3);
+        S[i] = (w >> 31) ? -1 : +1;
+    }
+}
+
+/* Eq. "hamiltonian": H = -sum over nearest-neighbour pairs of J_ij S_i S_j. */
+int or_energy(int dim, int L, const int8_t *J, const int8_t *S) {
+    int V = or_volume(dim, L), E = 0;
+    for (int i = 0; i < V; ++i)
+        for (int d = 0; d < dim; ++d)
+            E -= J[i * dim + d] * S[i] * S[neighbour(dim, L, i, d, +1)];
+    return E;
+}
+
+/* local field h_i = sum_j J_ij S_j over the 2*dim neighbours of i */
+static int local_field(int dim, int L, const int8_t *J, const int8_t *S, int i) {
+    int h = 0;
+    for (int d = 0; d < dim; ++d) {
+        int jp = neighbour(dim, L, i, d, +1);
+        int jm = neighbour(dim, L, i, d, -1);
+        h += J[i * dim + d] * S[jp];
+        h += J[jm * dim + d] * S[jm];
+    }
+    return h;
+}
+
+/* ---------------------------------------------------------------- energy bins */
+/* parity of the number of unsatisfied bonds (= parity of #negative couplings) */
+int or_parity(int dim, int L, const int8_t *J) {
+    int nb = or_nbonds(dim, L), neg = 0;
+    for (int j = 0; j < nb; ++j) neg += (J[j] < 0);
+    return neg & 1;
+}
+
+/* E = 2u - nb  =>  u = (E + nb)/2, bin = u >> 1 */
+int or_bin_of_energy(int dim, int L, int E) { return ((E + or_nbonds(dim, L)) / 2) >> 1; }
+int or_energy_of_bin(int dim, int L, int parity, int b) {
+    return 2 * (2 * b + parity) - or_nbonds(dim, L);
+}
+/* the largest attainable energy <= 0 ("E approx 0" of Sec. III) and its bin */
+int or_btop(int dim, int L, int parity) {
+    int uhalf = or_nbonds(dim, L) / 2;
+    int utop = ((uhalf & 1) == parity) ? uhalf : uhalf - 1;
+    return utop >> 1;
+}
+
+/* Deterministic start inside the MUCA range: from the random start, sweep the sites in
+ * lexicographic order flipping every spin whose flip lowers E, until E <= e_top. */
+int or_descend(int dim, int L, const int8_t *J, int8_t *S, int e_top, int32_t *E_io) {
+    int V = or_volume(dim, L), E = *E_io;
+    while (E > e_top) {
+        int flipped = 0;
+        for (int i = 0; i < V && E > e_top; ++i) {
+            int dE = 2 * S[i] * local_field(dim, L, J, S, i);
+            if (dE < 0) { S[i] = (int8_t)-S[i]; E += dE; flipped = 1; }
+        }
+        if (!flipped) return -1;
+    }
+    *E_io = E;
+    return 0;
+}
+
+/* ---------------------------------------------------------------- round trips */
+/* Sec. III: a round trip runs from the top of the energy range to the lowest energy
+ * E_g and back.  Phases: 0 = waiting for the first top visit, 1 = heading down,
+ * 2 = heading up.  Times are sweep indices.  One transition at most per check. */
+typedef struct {
+    int32_t phase, n_rt;
+    int64_t t_first, t_last;
+    int32_t e_min, e_g;
+    int32_t requeue, pad;
+} or_rt;
+
+static void rt_check(or_rt *rt, int E, int e_top, int e_bottom, uint64_t t) {
+    if (rt->phase == 0) {
+        if (E >= e_top) { rt->t_first = (int64_t)t; rt->phase = 1; }
+    } else if (rt->phase == 1) {
+        if (E <= e_bottom) rt->phase = 2;
+    } else {
+        if (E >= e_top) { rt->n_rt += 1; rt->t_last = (int64_t)t; rt->phase = 1; }
+    }
+}
+
+/* ---------------------------------------------------------------- MUCA chain */
+/* n_sweeps sweeps of single-spin-flip generalized Metropolis (Eq. "muca"), sites in
+ * lexicographic order.  thr is the chain's table, thr[b*8 + n] = threshold for a move
+ * from bin b at a site with n unsatisfied bonds (the move changes E by 2*(2*dim) - 4n).
+ * After every attempt: e_min update and (if count_rt) one round-trip check against
+ * rt->e_g.  After every sweep: hist[bin(E)] += 1 and e_trace[s] = E (if non-null). */
+int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
+                   const int8_t *J, int8_t *S, int32_t *E_io, uint64_t t0, uint64_t n_sweeps,
+                   const uint32_t *thr, int b_top, uint32_t *hist, or_rt *rt, int count_rt,
+                   int32_t *e_trace) {
+    int V = or_volume(dim, L), z = 2 * dim;
+    int E = *E_io;
+    int parity = ((E + or_nbonds(dim, L)) / 2) & 1;
+    int e_top = or_energy_of_bin(dim, L, parity, b_top);
+    for (uint64_t s = 0; s < n_sweeps; ++s) {
+        uint64_t t = t0 + s;
+        for (int i = 0; i < V; ++i) {
+            uint32_t r = rand_word(seed, (uint32_t)(i >> 2), (uint32_t)t, rid,
+                                   0u | (stream << 8), i & 3);
+            int h = local_field(dim, L, J, S, i);
+            int n_unsat = (z - S[i] * h) / 2;        /* S_i h_i = #sat - #unsat */
+            int dE = 2 * S[i] * h;                    /* = 2z - 4 n_unsat */
+            int b = or_bin_of_energy(dim, L, E);
+            uint32_t th = thr[(size_t)b * 8 + n_unsat];
+            int accept = (th == OR_ALWAYS) || (r < th);
+            if (accept) { S[i] = (int8_t)-S[i]; E += dE; }
+            if (E < rt->e_min) rt->e_min = E;
+            if (count_rt) rt_check(rt, E, e_top, rt->e_g, t);
+        }
+        hist[or_bin_of_energy(dim, L, E)] += 1;
+        if (e_trace) e_trace[s] = E;
+    }
+    if (count_rt && rt->e_min < rt->e_g) rt->requeue = 1;
+    *E_io = E;
+    return 0;
+}
+
+/* ---------------------------------------------------------------- weights */
+/* Quantised acceptance table from ln W (Eq. "muca"): p = W(E')/W(E) = exp(lnW(b')-lnW(b)).
+ * "always" when p >= 1, else min(floor(p*2^32), 2^32-2).  Moves out of [0, b_top] get 0. */
+void or_quantize(int dim, int b_top, const double *lnW, uint32_t *thr) {
+    for (int b = 0; b <= b_top; ++b) {
+        for (int n = 0; n < 8; ++n) {
+            uint32_t v = 0u;
+            int bn = b + dim - n;
+            if (n <= 2 * dim && bn >= 0 && bn <= b_top) {
+                double x = lnW[bn] - lnW[b];
+                if (x >= 0.0) {
+                    v = OR_ALWAYS;
+                } else {
+                    double q = floor(exp(x) * 4294967296.0);
+                    v = (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
+                }
+            }
+            thr[(size_t)b * 8 + n] = v;
+        }
+    }
+}
+
+/* Eq. "power_law": P_SH(E) = (E/(dE - E_g) + 1)^alpha, normalised to 1 at E = 0.
+ * Below E_g the profile is held at its value at E_g. */
+double or_ln_profile(int kind, double alpha, double pole_dE, int e_g, int E) {
+    if (kind != 1) return 0.0;
+    double Ec = (E < e_g) ? (double)e_g : (double)E;
+    return alpha * log(Ec / (pole_dE - (double)e_g) + 1.0);
+}
+
+/* One step of the weight iteration (Sec. II, the iterative procedure the paper takes
+ * from Janke 2003, with a shaped target histogram): W_{n+1}(E) = W_n(E) P_SH(E)/H_n(E),
+ * H_n taken as 1 in unvisited bins; then ln W is shifted to 0 at the top bin.  kind:
+ * 0 flat (P_SH = 1), 1 power law.  e_g is the lowest energy found so far. */
+void or_update_weights(int dim, int L, int parity, int b_top, int kind, double alpha,
+                       double pole_dE, int e_g, double *lnW, const uint32_t *hist) {
+    for (int b = 0; b <= b_top; ++b) {
+        int E = or_energy_of_bin(dim, L, parity, b);
+        double h = hist[b] > 0 ? (double)hist[b] : 1.0;
+        lnW[b] = lnW[b] + or_ln_profile(kind, alpha, pole_dE, e_g, E) - log(h);
+    }
+    double top = lnW[b_top];
+    for (int b = 0; b <= b_top; ++b) lnW[b] -= top;
+}
+
+/* Weights of a target ensemble from a density-of-states estimate ln Omega(b):
+ *   kind 0 flat       ln W = -ln Omega                           (Eq. "muca-weights")
+ *   kind 1 power law  ln W = ln P_SH - ln Omega                  (nonflat weight)
+ *   kind 2 1/k        ln W = -ln sum_{E_g <= E' <= E} Omega(E')  (Eq. "1/k"), E >= E_g;
+ *                     below E_g the flat form, matched at E_g
+ *   kind 3 canonical  ln W = -beta E
+ * then shifted to 0 at b_top. */
+void or_build_weights(int dim, int L, int parity, int b_top, int kind, double alpha,
+                      double pole_dE, double beta, int e_g, const double *lnOmega,
+                      double *lnW) {
+    int bg = or_bin_of_energy(dim, L, e_g);
+    if (bg < 0) bg = 0;
+    for (int b = 0; b <= b_top; ++b) {
+        int E = or_energy_of_bin(dim, L, parity, b);
+        if (kind == 0) {
+            lnW[b] = -lnOmega[b];
+        } else if (kind == 1) {
+            lnW[b] = or_ln_profile(1, alpha, pole_dE, e_g, E) - lnOmega[b];
+        } else if (kind == 2) {
+            if (b >= bg) {
+                double m = lnOmega[bg];
+                for (int c = bg; c <= b; ++c) if (lnOmega[c] > m) m = lnOmega[c];
+                double sum = 0.0;
+                for (int c = bg; c <= b; ++c) sum += exp(lnOmega[c] - m);
+                lnW[b] = -(m + log(sum));
+            }
+        } else {
+            lnW[b] = -beta * (double)E;
+        }
+    }
+    if (kind == 2) {
+        for (int b = 0; b < bg && b <= b_top; ++b)
+            lnW[b] = lnW[bg] + lnOmega[bg] - lnOmega[b];
+    }
+    double top = lnW[b_top];
+    for (int b = 0; b <= b_top; ++b) lnW[b] -= top;
+}
+
+/* ---------------------------------------------------------------- parallel tempering */
+/* Metropolis thresholds per slot (Sec. II, PT): a move raising E by dE = 2z - 4n
+ * (n < dim unsatisfied bonds) is accepted with p = exp(-beta_k dE).  Replica exchange
+ * (Eq. "temperatureexchange") between slots k, k+1 with E_k - E_{k+1} = 4d > 0 is
+ * accepted with p = exp(-(beta_{k+1} - beta_k) 4d).  Tables hold floor(p 2^32). */
+static uint32_t quantize_p(double p) {
+    if (p >= 1.0) return OR_ALWAYS;
+    double q = floor(p * 4294967296.0);
+    return (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
+}
+
+void or_pt_tables(int dim, int M, const double *beta, int dmax, uint32_t *thr_k,
+                  uint32_t *thr_pair) {
+    int z = 2 * dim;
+    for (int k = 0; k < M; ++k)
+        for (int n = 0; n < 8; ++n) {
+            uint32_t v = 0u;
+            if (n <= z) {
+                int dE = 2 * z - 4 * n;
+                v = (dE <= 0) ? OR_ALWAYS : quantize_p(exp(-beta[k] * (double)dE));
+            }
+            thr_k[k * 8 + n] = v;
+        }
+    for (int k = 0; k + 1 < M; ++k)
+        for (int d = 0; d <= dmax; ++d)
+            thr_pair[(size_t)k * (dmax + 1) + d] =
+                (d == 0) ? OR_ALWAYS
+                         : quantize_p(exp(-(beta[k + 1] - beta[k]) * 4.0 * (double)d));
+}
+
+/* the PT random word for one attempt: bit 31-m of r is bit (rid & 31) of word m */
+static uint32_t pt_rand(uint64_t seed, uint32_t rid, int slot, int i, uint64_t t) {
+    uint32_t r = 0u;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int g = 0; g < 8; ++g) {
+        uint32_t ctr[4] = {(uint32_t)(8 * i + g), (uint32_t)t, rid >> 5,
+                           4u | ((uint32_t)slot << 8)};
+        uint32_t w[4];
+        or_philox4x32_10(ctr, key, w);
+        for (int j = 0; j < 4; ++j) {
+            int m = 4 * g + j;
+            r |= ((w[j] >> (rid & 31)) & 1u) << (31 - m);
+        }
+    }
+    return r;
+}
+
+/* One realization, M replicas.  S holds the configuration currently at slot k in
+ * S[k*V ...]; E[k] its energy; label[k] the replica (configuration) number at slot k.
+ * Per sweep t: every slot gets a checkerboard Metropolis sweep (sites with even
+ * coordinate sum first, each colour in lexicographic order); then exchanges between
+ * slots (k, k+1) for k = t mod 2, t mod 2 + 2, ...; then, if count_rt, one round-trip
+ * check per replica with bottom e_g and top e_hot (Sec. III). rt is indexed by label. */
+int or_pt_sweeps(int dim, int L, uint64_t seed, uint32_t rid, int M, const int8_t *J,
+                 int8_t *S, int32_t *E, int32_t *label, uint64_t t0, uint64_t n_sweeps,
+                 const uint32_t *thr_k, const uint32_t *thr_pair, int dmax, or_rt *rt,
+                 int count_rt, int e_g, int e_hot, uint64_t *swap_acc) {
+    int V = or_volume(dim, L), z = 2 * dim;
+    if (L % 2) return -1;
+    int8_t *tmp = (int8_t *)malloc((size_t)V);
+    for (uint64_t s = 0; s < n_sweeps; ++s) {
+        uint64_t t = t0 + s;
+        for (int k = 0; k < M; ++k) {
+            int8_t *Sk = S + (size_t)k * V;
+            for (int colour = 0; colour < 2; ++colour) {
+                for (int i = 0; i < V; ++i) {
+                    int x = i % L, y = (i / L) % L, zz = (dim == 3) ? i / (L * L) : 0;
+                    if (((x + y + zz) & 1) != colour) continue;
+                    int h = local_field(dim, L, J, Sk, i);
+                    int n_unsat = (z - Sk[i] * h) / 2;
+                    int dE = 2 * Sk[i] * h;
+                    int accept;
+                    if (dE <= 0) {
+                        accept = 1;
+                    } else {
+                        uint32_t r = pt_rand(seed, rid, k, i, t);
+                        accept = r < thr_k[k * 8 + n_unsat];
+                    }
+                    if (accept) { Sk[i] = (int8_t)-Sk[i]; E[k] += dE; }
+                }
+            }
+        }
+        for (int k = (int)(t & 1); k + 1 < M; k += 2) {
+            int accept;
+            if (E[k + 1] >= E[k]) {
+                accept = 1;
+            } else {
+                int d = (E[k] - E[k + 1]) / 4;
+                uint32_t th = (d <= dmax) ? thr_pair[(size_t)k * (dmax + 1) + d] : 0u;
+                uint32_t r = rand_word(seed, (uint32_t)k, (uint32_t)t, rid, 1u, 0);
+                accept = (th == OR_ALWAYS) || (r < th);
+            }
+            if (accept) {
+                memcpy(tmp, S + (size_t)k * V, (size_t)V);
+                memcpy(S + (size_t)k * V, S + (size_t)(k + 1) * V, (size_t)V);
+                memcpy(S + (size_t)(k + 1) * V, tmp, (size_t)V);
+                int32_t te = E[k]; E[k] = E[k + 1]; E[k + 1] = te;
+                int32_t tl = label[k]; label[k] = label[k + 1]; label[k + 1] = tl;
+                if (swap_acc) swap_acc[k] += 1;
+            }
+        }
+        for (int k = 0; k < M; ++k) {
+            or_rt *r = &rt[label[k]];
+            if (E[k] < r->e_min) r->e_min = E[k];
+            if (count_rt) rt_check(r, E[k], e_hot, e_g, t);
+        }
+    }
+    free(tmp);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- brute force */
+/* Density of states g(u) (u = number of unsatisfied bonds) by enumerating every spin
+ * configuration with spin V-1 held up (the global flip doubles each count), in Gray-code
+ * order so that consecutive states differ by one spin. */
+int or_dos_bruteforce(int dim, int L, const int8_t *J, uint64_t *g) {
+    int V = or_volume(dim, L), nb = or_nbonds(dim, L);
+    if (V > 30) return -1;
+    int8_t *S = (int8_t *)malloc((size_t)V);
+    for (int i = 0; i < V; ++i) S[i] = 1;
+    for (int u = 0; u <= nb; ++u) g[u] = 0;
+    int E = or_energy(dim, L, J, S);
+    uint64_t nstates = 1ull << (V - 1);
+    g[(E + nb) / 2] += 2;
+    for (uint64_t k = 1; k < nstates; ++k) {
+        int i = __builtin_ctzll(k);          /* Gray code: flip the lowest set bit of k */
+        E += 2 * S[i] * local_field(dim, L, J, S, i);
+        S[i] = (int8_t)-S[i];
+        g[(E + nb) / 2] += 2;
+    }
+    free(S);
+    return 0;
+}
