@@ -1,0 +1,165 @@
+/*
+ * eamc.h -- C ABI of the GB300 library for generalized-ensemble Monte Carlo on the
+ * bimodal (+-J) Edwards-Anderson spin glass (Mueller, Schnabel, Janke,
+ * "Nonflat Histogram Techniques for Spin Glasses", arXiv:2011.08560).
+ *
+ * Model (Sec. II, Eq. "hamiltonian"): H = -sum_<ij> J_ij S_i S_j on an L^dim periodic
+ * simple-cubic lattice (dim = 3; dim = 2 is accepted for small test lattices), with 3V
+ * quenched couplings J = +-1 drawn with probability 1/2.
+ *
+ * Conventions shared by every entry point
+ *   - A context owns a batch of independent MUCA chains.  A chain is one disorder
+ *     realization (id `rid`) with one random stream (`stream`); two chains with the same
+ *     rid share their couplings.  Chains are numbered 0..ea_num_chains()-1 in the order
+ *     they were added.
+ *   - Site i = x + L*y (+ L*L*z); bond (i,d) joins i and i+e_d; per-bond arrays use
+ *     index i*dim + d.  Spins and couplings cross the ABI as int8 +1/-1.
+ *   - Energies are integers: E = 2u - dim*V with u the number of unsatisfied bonds.  The
+ *     bin of E is b = u >> 1 (u's parity is fixed per realization).  E_top is the largest
+ *     attainable E <= 0 ("E approx 0", Sec. III) and b_top its bin; MUCA chains stay at
+ *     E <= E_top (hard wall).
+ *   - Weights are ln W(b) in FP64, b = 0..b_top.  Acceptance thresholds are uint32:
+ *     thr[b*8 + n] is used for a move from bin b at a site with n unsatisfied bonds
+ *     (the move changes E by 2*(2*dim) - 4n); EA_ALWAYS accepts unconditionally, any
+ *     other value accepts iff the move's 32-bit random word r < thr.
+ *   - Random words come from Philox4x32-10 keyed by the context seed; counters are
+ *     (i>>2, sweep t, rid, stream<<8) for MUCA updates, so a chain's trajectory does not
+ *     depend on which other chains share the batch.
+ *   - All pointers in this header are HOST pointers to caller-owned buffers unless stated
+ *     otherwise; inputs are copied before the call returns, outputs are written before it
+ *     returns.  Device state lives in the context until ea_destroy.
+ *   - Every int-returning function returns EA_OK (0) or a negative EA_E* code and never
+ *     aborts; ea_last_error() gives the calling thread's last message.  A context is not
+ *     thread-safe: use one context per host thread / stream.
+ */
+#ifndef EAMC_H
+#define EAMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EA_OK 0
+#define EA_EINVAL (-1)   /* bad argument (size, range, null pointer) */
+#define EA_ENOMEM (-2)   /* device or host allocation failed */
+#define EA_ECUDA (-3)    /* a CUDA call failed; message in ea_last_error() */
+#define EA_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define EA_ESTATE (-5)   /* call not valid in the context's current state */
+
+#define EA_ALWAYS 0xFFFFFFFFu
+
+/* ensemble kinds */
+#define EA_FLAT 0       /* W ~ 1/Omega (Eq. "muca-weights") */
+#define EA_POWERLAW 1   /* W ~ P_SH/Omega, P_SH of Eq. "power_law" */
+#define EA_ONE_OVER_K 2 /* W ~ 1/k, k(E) = sum_{E_g<=E'<=E} Omega(E') (Eq. "1/k") */
+#define EA_CANON 3      /* W = exp(-beta E) (textbook Metropolis) */
+
+typedef struct ea_ctx ea_ctx;
+
+/* Round-trip record of one chain (Sec. III).  phase: 0 = waiting for the first visit of
+ * E_top, 1 = heading down to E_g, 2 = heading up to E_top.  A round trip completes at each
+ * top visit after a bottom visit.  t_first / t_last are sweep indices of the first top
+ * visit and of the last completed round trip (-1 if none); tau = (t_last-t_first)/n_rt.
+ * e_min is the lowest energy seen; requeue is set when e_min < e_g while counting
+ * (the paper's requeue on a lower energy, Sec. III). */
+typedef struct {
+    int32_t phase, n_rt;
+    int64_t t_first, t_last;
+    int32_t e_min, e_g;
+    int32_t requeue, pad;
+} ea_rt_stats;
+
+/* Static description of one chain. */
+typedef struct {
+    int32_t dim, L, b_top, parity; /* parity of u */
+    uint32_t rid, stream;
+    int32_t E, kind;                /* current energy, ensemble kind */
+    uint64_t t;                     /* sweeps done */
+} ea_chain_desc;
+
+const char *ea_last_error(void);
+
+/* Creates a context on CUDA device `device`; all work is queued on `cuda_stream` (a
+ * cudaStream_t, may be NULL for the legacy default stream; e.g. torch's current stream).
+ * `seed` keys every random word of the context.  *out receives the context. */
+int ea_create(ea_ctx **out, int device, void *cuda_stream, uint64_t seed);
+void ea_destroy(ea_ctx *ctx);
+
+/* a1 -- disorder and initial state (Sec. II: 3V couplings J = +-1 with p = 1/2, quenched).
+ * Appends n chains of linear size L (dim 2 or 3, 3 <= L <= 16) for realizations
+ * rid0, rid0+1, ... with random stream `stream`.  couplings_or_null: NULL to draw the
+ * couplings from the seed, else int8[n][dim*V] of +-1.  spins_or_null: NULL for random
+ * initial spins, else int8[n][V] of +-1.  Each chain then descends deterministically
+ * (lexicographic sweeps flipping spins that lower E) until E <= E_top.  Weights start at
+ * ln W = 0 (flat), ensemble EA_FLAT.  *first_chain (may be NULL) receives the index of the
+ * first new chain.  Returns EA_ESTATE if a descent gets stuck above E_top. */
+int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid0, uint32_t stream,
+                     const int8_t *couplings_or_null, const int8_t *spins_or_null,
+                     int *first_chain);
+
+int ea_num_chains(const ea_ctx *ctx);
+int ea_describe(ea_ctx *ctx, int chain0, int n, ea_chain_desc *out);
+
+/* a5 -- ensemble parameters of chains chain0..chain0+n-1: kind (EA_FLAT, EA_POWERLAW,
+ * EA_ONE_OVER_K, EA_CANON), power-law exponent alpha and pole offset pole_dE (Eq.
+ * "power_law", the paper's best values are -3.6 and 96), inverse temperature beta (canon).
+ * Only records the parameters used by muca_update_weights / muca_build_ensemble. */
+int muca_set_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
+                      double pole_dE, double beta);
+
+/* ln W input/output: lnW[c*stride + b] for chain c of the range, b = 0..b_top(c); stride
+ * >= the largest b_top+1 of the range.  set re-quantises the thresholds on the device. */
+int muca_set_weights(ea_ctx *ctx, int chain0, int n, const double *lnW, int stride);
+int muca_get_weights(ea_ctx *ctx, int chain0, int n, double *lnW, int stride);
+
+/* Thresholds input/output: thr[c*stride + b*8 + k], stride >= 8*(b_top+1).  set injects a
+ * table verbatim (parity testing); the next muca_set_weights / muca_update_weights /
+ * muca_build_ensemble overwrites it. */
+int muca_set_thresholds(ea_ctx *ctx, int chain0, int n, const uint32_t *thr, int stride);
+int muca_get_thresholds(ea_ctx *ctx, int chain0, int n, uint32_t *thr, int stride);
+
+/* Lowest-energy reference E_g per chain (bottom of a round trip, pole of the profile).
+ * e_g NULL takes each chain's lowest energy seen so far. */
+int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g);
+
+/* a2 + a3 -- n_sweeps sweeps of single-spin-flip generalized Metropolis (Eq. "muca",
+ * P_acc = min(1, W(E_new)/W(E_old))), sites in lexicographic order, for every chain of
+ * the context.  After every attempt: lowest-energy update and, if count_roundtrips, one
+ * round-trip check against E_top and E_g.  After every sweep: H(bin(E)) += 1.  Requires
+ * t + n_sweeps <= 2^32 for every chain.  Asynchronous on the context stream. */
+int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
+
+/* a4 -- one step of the weight iteration (Sec. II, iterative procedure after Janke 2003,
+ * with shaped histograms): ln W <- ln W + ln P_SH(E) - ln max(H(E), 1), shifted to 0 at
+ * b_top, with P_SH from the chain's kind (flat: 1, power law: Eq. "power_law" with E_g =
+ * lowest energy seen).  E_g is updated to that energy, the histogram is cleared and the
+ * thresholds are re-quantised.  Chains of kind EA_ONE_OVER_K / EA_CANON are untouched. */
+int muca_update_weights(ea_ctx *ctx);
+
+/* a5 -- rebuilds ln W of chains chain0..chain0+n-1 for a new ensemble from the density of
+ * states implied by the current weights (ln Omega = ln P_SH(current kind) - ln W), see
+ * EA_FLAT..EA_CANON, then re-quantises.  The new kind and parameters are recorded. */
+int muca_build_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
+                        double pole_dE, double beta);
+
+/* Histograms H[c*stride + b], b = 0..b_top(c); reset != 0 clears them afterwards. */
+int get_histograms(ea_ctx *ctx, int chain0, int n, uint32_t *out, int stride, int reset);
+
+/* Round-trip records; reset != 0 restarts counting (phase 0, n_rt 0, e_min = E). */
+int get_roundtrips(ea_ctx *ctx, int chain0, int n, ea_rt_stats *out, int reset);
+
+/* Spins spins[c*stride + i] (+-1, may be NULL), energies E[c] (may be NULL), sweeps t[c]
+ * (may be NULL). */
+int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stride, int32_t *E,
+              uint64_t *t);
+
+/* Waits for all queued work of the context. */
+int ea_synchronize(ea_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EAMC_H */

@@ -271,6 +271,7 @@ void or_build_weights(int dim, int L, int parity, int b_top, int kind, double al
                       double *lnW) {
     int bg = or_bin_of_energy(dim, L, e_g);
     if (bg < 0) bg = 0;
+    if (bg > b_top) bg = b_top;   /* an E_g above the range is read as E_top */
     for (int b = 0; b <= b_top; ++b) {
         int E = or_energy_of_bin(dim, L, parity, b);
         if (kind == 0) {

@@ -1,0 +1,631 @@
+// eamc_api.cu -- the C ABI declared in include/eamc.h: context, device arenas, and the
+// marshalling between caller buffers and the multi-spin-coded device layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eamc.h"
+#include "eamc_internal.cuh"
+#include "eamc_ctx.cuh"
+
+using namespace eamc;
+
+// ------------------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+int eamc::fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int eamc::cuda_fail(cudaError_t e, const char *what) {
+    return fail(EA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *ea_last_error(void) { return g_last_error.c_str(); }
+
+#define EA_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+// ------------------------------------------------------------------------------ helpers
+namespace {
+
+template <class T>
+int grow(T **ptr, size_t *cap, size_t used, size_t need, cudaStream_t st) {
+    if (need <= *cap) return EA_OK;
+    size_t ncap = std::max(need, *cap * 2);
+    T *np = nullptr;
+    if (cudaMalloc(&np, ncap * sizeof(T)) != cudaSuccess)
+        return fail(EA_ENOMEM, "device allocation of %zu bytes failed", ncap * sizeof(T));
+    cudaMemsetAsync(np, 0, ncap * sizeof(T), st);
+    if (*ptr && used) {
+        cudaError_t e = cudaMemcpyAsync(np, *ptr, used * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { cudaFree(np); return cuda_fail(e, "grow copy"); }
+    }
+    if (*ptr) {
+        cudaStreamSynchronize(st);
+        cudaFree(*ptr);
+    }
+    *ptr = np;
+    *cap = ncap;
+    return EA_OK;
+}
+
+// rows of per-chain tables <-> a dense [n][stride] staging array
+template <class T>
+__global__ void gather_rows(const T *__restrict__ table, const uint64_t *__restrict__ off,
+                            const int32_t *__restrict__ len, int n, int stride, int width,
+                            T *__restrict__ out) {
+    const int c = blockIdx.y;
+    if (c >= n) return;
+    const uint64_t o = off[c] * width;
+    const int l = len[c] * width;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < stride; k += gridDim.x * blockDim.x)
+        out[(size_t)c * stride + k] = (k < l) ? table[o + k] : T(0);
+}
+
+template <class T>
+__global__ void scatter_rows(T *__restrict__ table, const uint64_t *__restrict__ off,
+                             const int32_t *__restrict__ len, int n, int stride, int width,
+                             const T *__restrict__ in) {
+    const int c = blockIdx.y;
+    if (c >= n) return;
+    const uint64_t o = off[c] * width;
+    const int l = len[c] * width;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < l; k += gridDim.x * blockDim.x)
+        table[o + k] = in[(size_t)c * stride + k];
+}
+
+__global__ void unpack_spins(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ slot_of,
+                             int n, int stride, const uint32_t *__restrict__ spins,
+                             int8_t *__restrict__ out) {
+    const int c = blockIdx.y;
+    if (c >= n) return;
+    const int slot = slot_of[c];
+    const TileDesc td = tiles[slot / kTile];
+    const int lane = slot % kTile;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < td.V; i += gridDim.x * blockDim.x)
+        out[(size_t)c * stride + i] = ((spins[td.spin_off + i] >> lane) & 1u) ? int8_t(-1) : int8_t(1);
+}
+
+__global__ void set_eg_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                              const int32_t *__restrict__ slot_of, int n,
+                              const int32_t *__restrict__ e_g) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int slot = slot_of[c];
+    const TileDesc td = tiles[slot / kTile];
+    SlotState ss = slots[slot];
+    const int nb = td.dim * td.V;
+    const int eg = e_g ? e_g[c] : energy_of_bin(nb, ss.parity, ss.b_min);
+    ss.e_g = eg;
+    // bottom bin: the largest bin whose energy is <= e_g
+    int b = bin_of_energy(nb, eg);
+    while (b >= 0 && energy_of_bin(nb, ss.parity, b) > eg) --b;
+    ss.b_g = b;
+    slots[slot] = ss;
+}
+
+__global__ void set_params_kernel(SlotState *__restrict__ slots, const int32_t *__restrict__ slot_of,
+                                  int n, int kind, double alpha, double pole, double beta) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    SlotState &ss = slots[slot_of[c]];
+    ss.kind = kind;
+    ss.alpha = alpha;
+    ss.pole = pole;
+    ss.beta = beta;
+}
+
+__global__ void rt_out_kernel(const TileDesc *__restrict__ tiles, const SlotState *__restrict__ slots,
+                              const int32_t *__restrict__ slot_of, int n,
+                              ea_rt_stats *__restrict__ out, ea_chain_desc *__restrict__ desc) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int slot = slot_of[c];
+    const TileDesc td = tiles[slot / kTile];
+    const SlotState ss = slots[slot];
+    const int nb = td.dim * td.V;
+    if (out) {
+        ea_rt_stats r;
+        r.phase = ss.phase;
+        r.n_rt = ss.n_rt;
+        r.t_first = ss.t_first;
+        r.t_last = ss.t_last;
+        r.e_min = energy_of_bin(nb, ss.parity, ss.b_min);
+        r.e_g = ss.e_g;
+        r.requeue = ss.requeue;
+        r.pad = 0;
+        out[c] = r;
+    }
+    if (desc) {
+        ea_chain_desc d;
+        d.dim = td.dim;
+        d.L = td.L;
+        d.b_top = ss.b_top;
+        d.parity = ss.parity;
+        d.rid = ss.rid;
+        d.stream = ss.stream;
+        d.E = energy_of_bin(nb, ss.parity, ss.b);
+        d.kind = ss.kind;
+        d.t = ss.t;
+        desc[c] = d;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ context
+int eamc::ctx_scratch(ea_ctx *ctx, size_t bytes, void **out) {
+    if (bytes > ctx->scratch_cap) {
+        if (ctx->d_scratch) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->d_scratch);
+            ctx->d_scratch = nullptr;
+            ctx->scratch_cap = 0;
+        }
+        size_t cap = std::max(bytes, (size_t)1 << 20);
+        if (cudaMalloc(&ctx->d_scratch, cap) != cudaSuccess)
+            return fail(EA_ENOMEM, "scratch allocation of %zu bytes failed", cap);
+        ctx->scratch_cap = cap;
+    }
+    *out = ctx->d_scratch;
+    return EA_OK;
+}
+
+int eamc::ctx_check_range(ea_ctx *ctx, int chain0, int n) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (n < 0 || chain0 < 0 || chain0 + n > (int)ctx->chain_slot.size())
+        return fail(EA_EINVAL, "chain range [%d, %d) outside [0, %zu)", chain0, chain0 + n,
+                    ctx->chain_slot.size());
+    return EA_OK;
+}
+
+// uploads per-chain (slot, row offset, row length) of the range into scratch, returns
+// device pointers after `extra` bytes of caller scratch
+int eamc::ctx_range_meta(ea_ctx *ctx, int chain0, int n, size_t extra, void **scratch,
+                         int32_t **d_slot, uint64_t **d_off, int32_t **d_len) {
+    size_t a = (extra + 255) & ~(size_t)255;
+    size_t need = a + (size_t)n * (sizeof(int32_t) * 2 + sizeof(uint64_t)) + 512;
+    void *base;
+    int rc = ctx_scratch(ctx, need, &base);
+    if (rc) return rc;
+    char *p = (char *)base + a;
+    uint64_t *off = (uint64_t *)p;
+    int32_t *slot = (int32_t *)(p + (size_t)n * sizeof(uint64_t));
+    int32_t *len = slot + n;
+    std::vector<uint64_t> h_off(n);
+    std::vector<int32_t> h_slot(n), h_len(n);
+    for (int k = 0; k < n; ++k) {
+        const int c = chain0 + k;
+        h_slot[k] = ctx->chain_slot[c];
+        h_off[k] = ctx->chain_woff[c];
+        h_len[k] = ctx->chain_btop[c] + 1;
+    }
+    if (n > 0) {
+        EA_CUDA(cudaMemcpyAsync(off, h_off.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+        EA_CUDA(cudaMemcpyAsync(slot, h_slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        EA_CUDA(cudaMemcpyAsync(len, h_len.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        EA_CUDA(cudaStreamSynchronize(ctx->stream));  // host vectors go out of scope
+    }
+    *scratch = base;
+    *d_slot = slot;
+    *d_off = off;
+    *d_len = len;
+    return EA_OK;
+}
+
+int eamc::ctx_refresh_chains(ea_ctx *ctx) {
+    // host mirror of b_top per chain (needed for row lengths); read back the slot array
+    const size_t ns = ctx->tiles.size() * kTile;
+    std::vector<SlotState> h(ns);
+    if (ns) {
+        EA_CUDA(cudaMemcpyAsync(h.data(), ctx->d_slots, ns * sizeof(SlotState), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    for (size_t c = 0; c < ctx->chain_slot.size(); ++c) ctx->chain_btop[c] = h[ctx->chain_slot[c]].b_top;
+    return EA_OK;
+}
+
+extern "C" int ea_create(ea_ctx **out, int device, void *cuda_stream, uint64_t seed) {
+    if (!out) return fail(EA_EINVAL, "null output pointer");
+    int ndev = 0;
+    EA_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(EA_EINVAL, "device %d outside [0, %d)", device, ndev);
+    EA_CUDA(cudaSetDevice(device));
+    ea_ctx *ctx = new ea_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->seed = seed;
+    ctx->key = PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
+    cudaError_t e = cudaMalloc(&ctx->d_err, sizeof(int));
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaMalloc"); }
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    *out = ctx;
+    return EA_OK;
+}
+
+extern "C" void ea_destroy(ea_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    pt_release(ctx);
+    void *ptrs[] = {ctx->d_tiles, ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_lnW,
+                    ctx->d_hist,  ctx->d_thr,   ctx->d_scratch, ctx->d_err, ctx->d_Jin};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+}
+
+extern "C" int ea_num_chains(const ea_ctx *ctx) { return ctx ? (int)ctx->chain_slot.size() : 0; }
+
+extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid0, uint32_t stream,
+                                const int8_t *couplings, const int8_t *spins_in, int *first_chain) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (dim != 2 && dim != 3) return fail(EA_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+    if (L < 3 || L > 16) return fail(EA_EINVAL, "L must be in [3, 16] (got %d)", L);
+    if (n <= 0) return fail(EA_EINVAL, "n must be positive (got %d)", n);
+    if (stream >= (1u << 24)) return fail(EA_EINVAL, "stream must be < 2^24");
+    if (ctx->dim && ctx->dim != dim) return fail(EA_EINVAL, "a context holds a single dim");
+    EA_CUDA(cudaSetDevice(ctx->device));
+    const int V = volume_of(dim, L), B = rows_of(dim, L);
+    const int new_tiles = (n + kTile - 1) / kTile;
+    const int tile0 = (int)ctx->tiles.size();
+    const int chain_first = (int)ctx->chain_slot.size();
+
+    // layout of the new tiles
+    std::vector<TileDesc> nt(new_tiles);
+    size_t spin_used = ctx->spin_used, bond_used = ctx->bond_used, w_used = ctx->w_used;
+    for (int t = 0; t < new_tiles; ++t) {
+        TileDesc &td = nt[t];
+        td.dim = dim;
+        td.L = L;
+        td.V = V;
+        td.B = B;
+        td.n_active = std::min(kTile, n - t * kTile);
+        td.pad0 = 0;
+        td.w_base = w_used;
+        td.spin_off = spin_used;
+        td.bond_off = bond_used;
+        spin_used += (size_t)((V + 3) & ~3);
+        bond_used += (size_t)((dim * V + 3) & ~3);
+        w_used += (size_t)kTile * B;
+    }
+    const size_t ns_old = ctx->tiles.size() * kTile, ns_new = ns_old + (size_t)new_tiles * kTile;
+    int rc;
+    if ((rc = grow(&ctx->d_tiles, &ctx->tiles_cap, ctx->tiles.size(), ctx->tiles.size() + new_tiles, ctx->stream)) ||
+        (rc = grow(&ctx->d_slots, &ctx->slots_cap, ns_old, ns_new, ctx->stream)) ||
+        (rc = grow(&ctx->d_spins, &ctx->spins_cap, ctx->spin_used, spin_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_bonds, &ctx->bonds_cap, ctx->bond_used, bond_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_lnW, &ctx->lnW_cap, ctx->w_used, w_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_hist, &ctx->hist_cap, ctx->w_used, w_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_thr, &ctx->thr_cap, ctx->w_used * 8, w_used * 8, ctx->stream)))
+        return rc;
+    EA_CUDA(cudaMemcpyAsync(ctx->d_tiles + tile0, nt.data(), new_tiles * sizeof(TileDesc),
+                            cudaMemcpyHostToDevice, ctx->stream));
+    // per-slot identity (rid, stream, defaults)
+    std::vector<SlotState> hs((size_t)new_tiles * kTile);
+    for (size_t s = 0; s < hs.size(); ++s) {
+        SlotState &ss = hs[s];
+        std::memset(&ss, 0, sizeof ss);
+        const int k = (int)s;  // index within this group
+        ss.rid = rid0 + (uint32_t)std::min(k, n - 1);
+        ss.stream = stream;
+        ss.kind = EA_FLAT;
+        ss.alpha = -3.6;
+        ss.pole = 96.0;
+        ss.beta = 1.0;
+    }
+    EA_CUDA(cudaMemcpyAsync(ctx->d_slots + ns_old, hs.data(), hs.size() * sizeof(SlotState),
+                            cudaMemcpyHostToDevice, ctx->stream));
+    // optional caller arrays
+    const int8_t *dJ = nullptr, *dS = nullptr;
+    void *scratch = nullptr;
+    const size_t jbytes = couplings ? (size_t)n * dim * V : 0, sbytes = spins_in ? (size_t)n * V : 0;
+    if (jbytes + sbytes) {
+        if ((rc = ctx_scratch(ctx, jbytes + sbytes + 256, &scratch))) return rc;
+        if (couplings) {
+            dJ = (const int8_t *)scratch;
+            EA_CUDA(cudaMemcpyAsync((void *)dJ, couplings, jbytes, cudaMemcpyHostToDevice, ctx->stream));
+        }
+        if (spins_in) {
+            dS = (const int8_t *)scratch + ((jbytes + 127) & ~(size_t)127);
+            EA_CUDA(cudaMemcpyAsync((void *)dS, spins_in, sbytes, cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
+    EA_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    EA_CUDA(launch_init(ctx->d_tiles, tile0, new_tiles, dim, ctx->d_slots, ctx->d_spins,
+                        ctx->d_bonds, dJ, dS, 0, ctx->key, ctx->d_err, ctx->stream));
+    int herr = 0;
+    EA_CUDA(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    // commit the new tiles
+    ctx->dim = dim;
+    for (const TileDesc &td : nt) ctx->tiles.push_back(td);
+    ctx->spin_used = spin_used;
+    ctx->bond_used = bond_used;
+    ctx->w_used = w_used;
+    ctx->max_V = std::max(ctx->max_V, V);
+    for (int k = 0; k < n; ++k) {
+        const int slot = (tile0 + k / kTile) * kTile + k % kTile;
+        ctx->chain_slot.push_back(slot);
+        ctx->chain_woff.push_back(nt[k / kTile].w_base + (uint64_t)(k % kTile) * B);
+        ctx->chain_btop.push_back(0);
+    }
+    if ((rc = ctx_refresh_chains(ctx))) return rc;
+    // flat weights (ln W = 0 already) -> thresholds
+    EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW,
+                            ctx->d_thr, ctx->stream));
+    if (first_chain) *first_chain = chain_first;
+    if (herr) return fail(EA_ESTATE, "descent to E_top got stuck in a local minimum");
+    return EA_OK;
+}
+
+extern "C" int ea_describe(ea_ctx *ctx, int chain0, int n, ea_chain_desc *out) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc) return rc;
+    if (!out) return fail(EA_EINVAL, "null output");
+    if (n == 0) return EA_OK;
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, (size_t)n * sizeof(ea_chain_desc), &scr, &d_slot, &d_off, &d_len)))
+        return rc;
+    ea_chain_desc *d_out = (ea_chain_desc *)scr;
+    rt_out_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_tiles, ctx->d_slots, d_slot, n,
+                                                            nullptr, d_out);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(ea_chain_desc), cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_set_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
+                                 double pole_dE, double beta) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc) return rc;
+    if (kind < EA_FLAT || kind > EA_CANON) return fail(EA_EINVAL, "unknown ensemble kind %d", kind);
+    if (kind == EA_POWERLAW && !(pole_dE > 0.0)) return fail(EA_EINVAL, "pole_dE must be > 0");
+    if (n == 0) return EA_OK;
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, 0, &scr, &d_slot, &d_off, &d_len))) return rc;
+    set_params_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_slots, d_slot, n, kind, alpha,
+                                                                pole_dE, beta);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+static int max_len(ea_ctx *ctx, int chain0, int n) {
+    int m = 0;
+    for (int k = 0; k < n; ++k) m = std::max(m, ctx->chain_btop[chain0 + k] + 1);
+    return m;
+}
+
+template <class T>
+static int table_io(ea_ctx *ctx, int chain0, int n, T *table, int width, T *host, int stride,
+                    bool to_device) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc) return rc;
+    if (!host) return fail(EA_EINVAL, "null buffer");
+    if (n == 0) return EA_OK;
+    if (stride < max_len(ctx, chain0, n) * width)
+        return fail(EA_EINVAL, "stride %d shorter than a row (%d)", stride, max_len(ctx, chain0, n) * width);
+    const size_t bytes = (size_t)n * stride * sizeof(T);
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, bytes, &scr, &d_slot, &d_off, &d_len))) return rc;
+    T *stage = (T *)scr;
+    dim3 grid((stride + 255) / 256, n);
+    if (to_device) {
+        EA_CUDA(cudaMemcpyAsync(stage, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        scatter_rows<T><<<grid, 256, 0, ctx->stream>>>(table, d_off, d_len, n, stride, width, stage);
+        EA_CUDA(cudaGetLastError());
+        EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    } else {
+        gather_rows<T><<<grid, 256, 0, ctx->stream>>>(table, d_off, d_len, n, stride, width, stage);
+        EA_CUDA(cudaGetLastError());
+        EA_CUDA(cudaMemcpyAsync(host, stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return EA_OK;
+}
+
+extern "C" int muca_set_weights(ea_ctx *ctx, int chain0, int n, const double *lnW, int stride) {
+    int rc = table_io<double>(ctx, chain0, n, ctx ? ctx->d_lnW : nullptr, 1, const_cast<double *>(lnW),
+                              stride, true);
+    if (rc) return rc;
+    EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW, ctx->d_thr,
+                            ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_get_weights(ea_ctx *ctx, int chain0, int n, double *lnW, int stride) {
+    return table_io<double>(ctx, chain0, n, ctx ? ctx->d_lnW : nullptr, 1, lnW, stride, false);
+}
+
+extern "C" int muca_set_thresholds(ea_ctx *ctx, int chain0, int n, const uint32_t *thr, int stride) {
+    int rc = table_io<uint32_t>(ctx, chain0, n, ctx ? ctx->d_thr : nullptr, 8, const_cast<uint32_t *>(thr),
+                                stride, true);
+    if (rc) return rc;
+    EA_CUDA(launch_enforce_walls(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_thr, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_get_thresholds(ea_ctx *ctx, int chain0, int n, uint32_t *thr, int stride) {
+    return table_io<uint32_t>(ctx, chain0, n, ctx ? ctx->d_thr : nullptr, 8, thr, stride, false);
+}
+
+extern "C" int get_histograms(ea_ctx *ctx, int chain0, int n, uint32_t *out, int stride, int reset) {
+    int rc = table_io<uint32_t>(ctx, chain0, n, ctx ? ctx->d_hist : nullptr, 1, out, stride, false);
+    if (rc || !reset || n == 0) return rc;
+    // clear the rows of the range: scatter zeros
+    const size_t bytes = (size_t)n * stride * sizeof(uint32_t);
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, bytes, &scr, &d_slot, &d_off, &d_len))) return rc;
+    EA_CUDA(cudaMemsetAsync(scr, 0, bytes, ctx->stream));
+    dim3 grid((stride + 255) / 256, n);
+    scatter_rows<uint32_t><<<grid, 256, 0, ctx->stream>>>(ctx->d_hist, d_off, d_len, n, stride, 1,
+                                                          (const uint32_t *)scr);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc || n == 0) return rc;
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, (size_t)n * sizeof(int32_t), &scr, &d_slot, &d_off, &d_len)))
+        return rc;
+    int32_t *d_eg = nullptr;
+    if (e_g) {
+        d_eg = (int32_t *)scr;
+        EA_CUDA(cudaMemcpyAsync(d_eg, e_g, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    set_eg_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_tiles, ctx->d_slots, d_slot, n, d_eg);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains: call ea_init_disorder first");
+    if (n_sweeps > (1ull << 32) || ctx->max_t_host + n_sweeps > (1ull << 32))
+        return fail(EA_EINVAL, "sweep counter would exceed 2^32");
+    EA_CUDA(launch_sweeps(ctx->d_tiles, (int)ctx->tiles.size(), ctx->dim, ctx->max_V, ctx->d_slots,
+                          ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, n_sweeps, ctx->key,
+                          count_roundtrips, ctx->stream));
+    ctx->max_t_host += n_sweeps;
+    return EA_OK;
+}
+
+extern "C" int muca_update_weights(ea_ctx *ctx) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains");
+    const int nt = (int)ctx->tiles.size();
+    EA_CUDA(launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->stream));
+    EA_CUDA(launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream));
+    return EA_OK;
+}
+
+static int select_range(ea_ctx *ctx, int chain0, int n, uint8_t **d_sel) {
+    const size_t ns = ctx->tiles.size() * kTile;
+    std::vector<uint8_t> sel(ns, 0);
+    for (int k = 0; k < n; ++k) sel[ctx->chain_slot[chain0 + k]] = 1;
+    void *scr;
+    int rc = ctx_scratch(ctx, ns + 64, &scr);
+    if (rc) return rc;
+    EA_CUDA(cudaMemcpyAsync(scr, sel.data(), ns, cudaMemcpyHostToDevice, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    *d_sel = (uint8_t *)scr;
+    return EA_OK;
+}
+
+extern "C" int muca_build_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
+                                   double pole_dE, double beta) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc || n == 0) return rc;
+    if (kind < EA_FLAT || kind > EA_CANON) return fail(EA_EINVAL, "unknown ensemble kind %d", kind);
+    uint8_t *d_sel;
+    if ((rc = select_range(ctx, chain0, n, &d_sel))) return rc;
+    const int nt = (int)ctx->tiles.size();
+    EA_CUDA(launch_build_ensemble(ctx->d_tiles, nt, ctx->d_slots, d_sel, kind, alpha, pole_dE, beta,
+                                  ctx->d_lnW, ctx->stream));
+    EA_CUDA(launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int get_roundtrips(ea_ctx *ctx, int chain0, int n, ea_rt_stats *out, int reset) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc || n == 0) return rc;
+    if (!out) return fail(EA_EINVAL, "null output");
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, (size_t)n * sizeof(ea_rt_stats), &scr, &d_slot, &d_off, &d_len)))
+        return rc;
+    ea_rt_stats *d_out = (ea_rt_stats *)scr;
+    rt_out_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_tiles, ctx->d_slots, d_slot, n, d_out,
+                                                            nullptr);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(ea_rt_stats), cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (reset) {
+        uint8_t *d_sel;
+        if ((rc = select_range(ctx, chain0, n, &d_sel))) return rc;
+        EA_CUDA(launch_reset_rt(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, d_sel, ctx->stream));
+        EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return EA_OK;
+}
+
+extern "C" int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stride, int32_t *E,
+                         uint64_t *t) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc || n == 0) return rc;
+    int maxV = 0;
+    for (int k = 0; k < n; ++k) {
+        const int slot = ctx->chain_slot[chain0 + k];
+        maxV = std::max(maxV, ctx->tiles[slot / kTile].V);
+    }
+    if (spins && stride < maxV) return fail(EA_EINVAL, "spin stride %d < V = %d", stride, maxV);
+    const size_t sbytes = spins ? (size_t)n * stride : 0;
+    const size_t dbytes = (size_t)n * sizeof(ea_chain_desc);
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, ((sbytes + 255) & ~(size_t)255) + dbytes, &scr, &d_slot, &d_off,
+                             &d_len)))
+        return rc;
+    int8_t *d_sp = (int8_t *)scr;
+    ea_chain_desc *d_desc = (ea_chain_desc *)((char *)scr + ((sbytes + 255) & ~(size_t)255));
+    if (spins) {
+        dim3 grid((maxV + 255) / 256, n);
+        unpack_spins<<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, d_slot, n, stride, ctx->d_spins, d_sp);
+        EA_CUDA(cudaGetLastError());
+        EA_CUDA(cudaMemcpyAsync(spins, d_sp, sbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    rt_out_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_tiles, ctx->d_slots, d_slot, n, nullptr,
+                                                            d_desc);
+    EA_CUDA(cudaGetLastError());
+    std::vector<ea_chain_desc> h(n);
+    EA_CUDA(cudaMemcpyAsync(h.data(), d_desc, dbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < n; ++k) {
+        if (E) E[k] = h[k].E;
+        if (t) t[k] = h[k].t;
+    }
+    return EA_OK;
+}
+
+extern "C" int ea_synchronize(ea_ctx *ctx) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    EA_CUDA(cudaGetLastError());
+    return EA_OK;
+}

@@ -1,0 +1,78 @@
+// eamc_internal.cuh -- device data layout shared by the kernels and the C-ABI layer.
+//
+// Chains are packed 32 to a tile (one warp): bit `lane` of every spin / bond word of a
+// tile belongs to the tile's chain `lane`.  All chains of a tile have the same dim and L.
+//
+//   spins  u32[spin_off + i]          site i, bit lane = spin of chain lane is -1
+//   bonds  u32[bond_off + i*dim + d]  bond (i, d), bit lane = coupling of chain lane is -1
+//   lnW    f64[w_base + lane*B + b]   ln W(b), b = 0..b_top(chain)
+//   hist   u32[w_base + lane*B + b]   H(b)
+//   thr    u32[(w_base + lane*B + b)*8 + n]  acceptance threshold from bin b, n unsatisfied
+//   slots  SlotState[tile*32 + lane]  per-chain scalars
+#pragma once
+#include <cstdint>
+
+#include "philox.cuh"
+
+namespace eamc {
+
+constexpr uint32_t kAlways = 0xFFFFFFFFu;
+constexpr int kTile = 32;
+constexpr int kNoBottom = -1;  // b_g when no E_g is known yet: never reached
+
+struct TileDesc {
+    int32_t dim, L, V, B;  // B = table rows per chain = largest b_top + 1 for this (dim, L)
+    int32_t n_active, pad0;
+    uint64_t w_base;       // element offset of lane 0's lnW / hist rows
+    uint64_t spin_off;     // word offset of the tile's V spin words
+    uint64_t bond_off;     // word offset of the tile's dim*V bond words
+};
+
+struct SlotState {
+    int32_t b, parity, b_top, b_min;  // current bin, parity of u, top bin, lowest bin seen
+    int32_t b_g, e_g;                 // bottom of a round trip (bin, energy)
+    int32_t phase, n_rt;              // round-trip state machine
+    int64_t t_first, t_last;
+    uint64_t t;                       // sweeps done
+    uint32_t rid, stream;
+    int32_t kind, active;
+    int32_t requeue, pad0;
+    double alpha, pole, beta;         // ensemble parameters
+};
+
+__host__ __device__ inline int volume_of(int dim, int L) { return dim == 2 ? L * L : L * L * L; }
+__host__ __device__ inline int rows_of(int dim, int L) {
+    return ((dim * volume_of(dim, L)) / 2 >> 1) + 1;
+}
+__host__ __device__ inline int energy_of_bin(int nb, int parity, int b) {
+    return 2 * (2 * b + parity) - nb;
+}
+__host__ __device__ inline int bin_of_energy(int nb, int E) { return ((E + nb) / 2) >> 1; }
+__host__ __device__ inline int top_bin(int nb, int parity) {
+    const int uhalf = nb / 2;
+    const int utop = ((uhalf & 1) == parity) ? uhalf : uhalf - 1;
+    return utop >> 1;
+}
+
+// kernel launchers (muca_kernels.cu)
+cudaError_t launch_init(const TileDesc *d_tiles, int tile0, int n_tiles, int dim,
+                        SlotState *d_slots, uint32_t *d_spins, uint32_t *d_bonds,
+                        const int8_t *d_J, const int8_t *d_S, int in_row0, PhiloxKey key,
+                        int *d_err, cudaStream_t st);
+cudaError_t launch_sweeps(const TileDesc *d_tiles, int n_tiles, int dim, int max_V,
+                          SlotState *d_slots, uint32_t *d_spins, const uint32_t *d_bonds,
+                          const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
+                          PhiloxKey key, int count_rt, cudaStream_t st);
+cudaError_t launch_quantize(const TileDesc *d_tiles, int n_tiles, const SlotState *d_slots,
+                            const double *d_lnW, uint32_t *d_thr, cudaStream_t st);
+cudaError_t launch_enforce_walls(const TileDesc *d_tiles, int n_tiles, const SlotState *d_slots,
+                                 uint32_t *d_thr, cudaStream_t st);
+cudaError_t launch_update_weights(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
+                                  double *d_lnW, uint32_t *d_hist, cudaStream_t st);
+cudaError_t launch_build_ensemble(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
+                                  const uint8_t *d_sel, int kind, double alpha, double pole,
+                                  double beta, double *d_lnW, cudaStream_t st);
+cudaError_t launch_reset_rt(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
+                            const uint8_t *d_sel, cudaStream_t st);
+
+}  // namespace eamc

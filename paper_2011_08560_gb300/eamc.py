@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libeamc.so (include/eamc.h).
+
+Argument marshalling only: every step of the Monte Carlo path runs in the CUDA library.
+The functions keep the C names; ``Context`` wraps one ``ea_ctx``.  PyTorch is used only to
+hand over the current CUDA stream.  There is no CPU fallback: importing this module on a
+machine where the library cannot be loaded raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from .build import LIB
+
+EA_OK, EA_EINVAL, EA_ENOMEM, EA_ECUDA, EA_ETIMEOUT, EA_ESTATE = 0, -1, -2, -3, -4, -5
+EA_ALWAYS = 0xFFFFFFFF
+EA_FLAT, EA_POWERLAW, EA_ONE_OVER_K, EA_CANON = 0, 1, 2, 3
+
+
+class EamcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"eamc error {code}: {msg}")
+        self.code = code
+
+
+class ea_rt_stats(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int32), ("n_rt", ctypes.c_int32),
+                ("t_first", ctypes.c_int64), ("t_last", ctypes.c_int64),
+                ("e_min", ctypes.c_int32), ("e_g", ctypes.c_int32),
+                ("requeue", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class ea_chain_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("L", ctypes.c_int32), ("b_top", ctypes.c_int32),
+                ("parity", ctypes.c_int32), ("rid", ctypes.c_uint32),
+                ("stream", ctypes.c_uint32), ("E", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("t", ctypes.c_uint64)]
+
+
+class ea_pt_stats(ctypes.Structure):
+    _fields_ = [("n_rt", ctypes.c_int32), ("phase", ctypes.c_int32),
+                ("t_first", ctypes.c_int64), ("t_last", ctypes.c_int64),
+                ("e_min", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+P = ctypes.c_void_p
+_i, _u32, _u64, _f64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+
+# name -> (restype, argtypes); the same names as include/eamc.h
+SIGNATURES = {
+    "ea_last_error": (ctypes.c_char_p, []),
+    "ea_create": (_i, [ctypes.POINTER(P), _i, P, _u64]),
+    "ea_destroy": (None, [P]),
+    "ea_init_disorder": (_i, [P, _i, _i, _i, _u32, _u32, P, P, ctypes.POINTER(_i)]),
+    "ea_num_chains": (_i, [P]),
+    "ea_describe": (_i, [P, _i, _i, P]),
+    "muca_set_ensemble": (_i, [P, _i, _i, _i, _f64, _f64, _f64]),
+    "muca_set_weights": (_i, [P, _i, _i, P, _i]),
+    "muca_get_weights": (_i, [P, _i, _i, P, _i]),
+    "muca_set_thresholds": (_i, [P, _i, _i, P, _i]),
+    "muca_get_thresholds": (_i, [P, _i, _i, P, _i]),
+    "muca_set_eg": (_i, [P, _i, _i, P]),
+    "muca_run_sweeps": (_i, [P, _u64, _i]),
+    "muca_update_weights": (_i, [P]),
+    "muca_build_ensemble": (_i, [P, _i, _i, _i, _f64, _f64, _f64]),
+    "get_histograms": (_i, [P, _i, _i, P, _i, _i]),
+    "get_roundtrips": (_i, [P, _i, _i, P, _i]),
+    "get_state": (_i, [P, _i, _i, P, _i, P, P]),
+    "ea_synchronize": (_i, [P]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libeamc.so (built in-tree by __graft_entry__.build()); raises if missing."""
+    global _lib
+    if _lib is None:
+        if not Path(LIB).exists():
+            raise ImportError(f"{LIB} is missing: build it with __graft_entry__.build()")
+        _lib = ctypes.CDLL(str(LIB))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def check(rc: int) -> int:
+    if rc != EA_OK:
+        raise EamcError(rc, lib().ea_last_error().decode())
+    return rc
+
+
+def _p(a: np.ndarray):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "buffers must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One ea_ctx: a batch of MUCA chains resident on a CUDA device."""
+
+    def __init__(self, seed: int, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        check(lib().ea_create(ctypes.byref(self._h), device, st, seed))
+        self.seed = seed
+
+    def close(self):
+        if self._h:
+            lib().ea_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # a1
+    def init_disorder(self, dim: int, L: int, n: int, rid0: int = 0, stream: int = 0,
+                      couplings: np.ndarray | None = None, spins: np.ndarray | None = None) -> int:
+        first = ctypes.c_int(-1)
+        J = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
+        S = None if spins is None else np.ascontiguousarray(spins, dtype=np.int8)
+        check(lib().ea_init_disorder(self._h, dim, L, n, rid0, stream, _p(J), _p(S),
+                                     ctypes.byref(first)))
+        return first.value
+
+    def num_chains(self) -> int:
+        return lib().ea_num_chains(self._h)
+
+    def describe(self, chain0: int = 0, n: int | None = None):
+        n = self.num_chains() - chain0 if n is None else n
+        out = (ea_chain_desc * n)()
+        check(lib().ea_describe(self._h, chain0, n, out))
+        return [{f: getattr(d, f) for f, _ in ea_chain_desc._fields_} for d in out]
+
+    # a5
+    def set_ensemble(self, chain0: int, n: int, kind: int, alpha: float = -3.6,
+                     pole: float = 96.0, beta: float = 1.0):
+        check(lib().muca_set_ensemble(self._h, chain0, n, kind, alpha, pole, beta))
+
+    def build_ensemble(self, chain0: int, n: int, kind: int, alpha: float = -3.6,
+                       pole: float = 96.0, beta: float = 1.0):
+        check(lib().muca_build_ensemble(self._h, chain0, n, kind, alpha, pole, beta))
+
+    def _rows(self, chain0, n):
+        return max(d["b_top"] for d in self.describe(chain0, n)) + 1
+
+    def set_weights(self, chain0: int, lnW: np.ndarray):
+        lnW = np.ascontiguousarray(np.atleast_2d(lnW), dtype=np.float64)
+        check(lib().muca_set_weights(self._h, chain0, lnW.shape[0], _p(lnW), lnW.shape[1]))
+
+    def get_weights(self, chain0: int = 0, n: int | None = None, rows: int | None = None):
+        n = self.num_chains() - chain0 if n is None else n
+        rows = self._rows(chain0, n) if rows is None else rows
+        out = np.zeros((n, rows), dtype=np.float64)
+        check(lib().muca_get_weights(self._h, chain0, n, _p(out), rows))
+        return out
+
+    def set_thresholds(self, chain0: int, thr: np.ndarray):
+        thr = np.ascontiguousarray(np.atleast_2d(thr), dtype=np.uint32)
+        check(lib().muca_set_thresholds(self._h, chain0, thr.shape[0], _p(thr), thr.shape[1]))
+
+    def get_thresholds(self, chain0: int = 0, n: int | None = None, rows: int | None = None):
+        n = self.num_chains() - chain0 if n is None else n
+        rows = self._rows(chain0, n) if rows is None else rows
+        out = np.zeros((n, rows * 8), dtype=np.uint32)
+        check(lib().muca_get_thresholds(self._h, chain0, n, _p(out), rows * 8))
+        return out
+
+    def set_eg(self, chain0: int, n: int, e_g: np.ndarray | None = None):
+        arr = None if e_g is None else np.ascontiguousarray(e_g, dtype=np.int32)
+        check(lib().muca_set_eg(self._h, chain0, n, _p(arr)))
+
+    # a2 + a3
+    def run_sweeps(self, n_sweeps: int, count_roundtrips: bool = False):
+        check(lib().muca_run_sweeps(self._h, n_sweeps, int(count_roundtrips)))
+
+    # a4
+    def update_weights(self):
+        check(lib().muca_update_weights(self._h))
+
+    def histograms(self, chain0: int = 0, n: int | None = None, reset: bool = False,
+                   rows: int | None = None):
+        n = self.num_chains() - chain0 if n is None else n
+        rows = self._rows(chain0, n) if rows is None else rows
+        out = np.zeros((n, rows), dtype=np.uint32)
+        check(lib().get_histograms(self._h, chain0, n, _p(out), rows, int(reset)))
+        return out
+
+    def roundtrips(self, chain0: int = 0, n: int | None = None, reset: bool = False):
+        n = self.num_chains() - chain0 if n is None else n
+        out = (ea_rt_stats * n)()
+        check(lib().get_roundtrips(self._h, chain0, n, out, int(reset)))
+        return [{f: getattr(r, f) for f, _ in ea_rt_stats._fields_ if f != "pad"} for r in out]
+
+    def state(self, chain0: int = 0, n: int | None = None, spins: bool = True):
+        n = self.num_chains() - chain0 if n is None else n
+        descs = self.describe(chain0, n)
+        V = max(d["L"] ** d["dim"] for d in descs)
+        S = np.zeros((n, V), dtype=np.int8) if spins else None
+        E = np.zeros(n, dtype=np.int32)
+        t = np.zeros(n, dtype=np.uint64)
+        check(lib().get_state(self._h, chain0, n, _p(S), V, _p(E), _p(t)))
+        return S, E, t
+
+    def synchronize(self):
+        check(lib().ea_synchronize(self._h))
