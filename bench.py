@@ -1,0 +1,350 @@
+"""Benchmark: batched power-law / flat MUCA on the 3D +-J EA spin glass, one JSON line.
+
+Workload: L=6, 1024 disorder realizations, each run as a flat-MUCA chain and as a
+power-law-MUCA chain (alpha=-3.6, Delta E=96) -> 2048 chains in one context, packed 32 per
+warp.  One step = one pass of the hot path over the batch: `sweeps_per_step` sweeps of
+generalized Metropolis with histogram, lowest-energy and round-trip measurement
+(muca_run_sweeps), then one weight-iteration update with re-quantisation
+(muca_update_weights).  Metric: spin-flip attempts per ns (whole job), with round trips per
+second beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (plain C, one chain at a time, all host cores) on a
+bounded sample of the same workload.  Under torchrun every rank runs its own 1024
+realizations (disjoint realization ids, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2011_08560_gb300.workloads import HEADLINE  # noqa: E402
+
+METRIC = "spin-flip attempts/ns"
+UNIT = "attempts/ns"
+# algorithmic integer lane-operations per spin-flip attempt ("roofline"):
+# 10 (quarter of a Philox4x32-10 call) + 3.5 (bit-sliced local field, 32 chains per word,
+# plus extraction) + 3 (threshold fetch and compare) + 2 (flip and energy update)
+# + 3 (lowest energy and round-trip check)
+ALG_OPS_PER_ATTEMPT = 21.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sweeps-per-step", type=int, default=10_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ oracle (CPU)
+def _oracle_worker(args):
+    import numpy as np
+
+    import oracle
+    dim, L, seed, rid, stream, kind, sweeps = args
+    c = oracle.Chain(dim, L, seed, rid, stream)
+    lnW = np.zeros(c.b_top + 1)
+    t0 = time.perf_counter()
+    c.sweeps(sweeps, oracle.quantize(dim, lnW), count_rt=True)
+    lnW = oracle.update_weights(dim, L, c.parity, kind, HEADLINE.alpha, HEADLINE.pole,
+                                c.rt.e_min, lnW, c.hist)
+    dt = time.perf_counter() - t0
+    return c.V * sweeps, dt, c.rt.n_rt
+
+
+def oracle_sample(target_s: float = 15.0, cores: int | None = None):
+    """Times the oracle on all host cores on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    cores = cores or os.cpu_count() or 1
+    W = HEADLINE
+    # calibrate one chain
+    calib = _oracle_worker((W.dim, W.L, W.seed, 0, 0, 0, 200))
+    per_sweep = calib[1] / 200
+    chains = 2 * cores
+    sweeps = max(50, int(target_s * cores / (chains * per_sweep)))
+    jobs = [(W.dim, W.L, W.seed, k // 2, k % 2, k % 2, sweeps) for k in range(chains)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    attempts = sum(r[0] for r in res)
+    return {"value": attempts / (wall * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{chains} chains (flat and power law alternating) x {sweeps} sweeps + one "
+                      f"weight update each, L={W.L}, {wall:.1f} s wall on {cores} processes",
+            "round_trips": sum(r[2] for r in res), "wall_s": wall}
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = ROOT / "gpurun_out" / f"clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        self.path.parent.mkdir(exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not self.path.exists():
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.path.read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def build_context(eamc, rank: int, stream_ptr: int):
+    W = HEADLINE
+    ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
+    n = W.n_real
+    rid0 = rank * n
+    ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=0)          # flat MUCA chains
+    ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=1)          # power-law MUCA chains
+    ctx.set_ensemble(0, n, eamc.EA_FLAT)
+    ctx.set_ensemble(n, n, eamc.EA_POWERLAW, W.alpha, W.pole)
+    return ctx
+
+
+def total_rt(ctx):
+    return sum(r["n_rt"] for r in ctx.roundtrips())
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    W = HEADLINE
+    S = args.sweeps_per_step
+    stream = torch.cuda.Stream()
+    ctx = build_context(eamc, rank, stream.cuda_stream)
+    n_chains = ctx.num_chains()
+    V = W.L ** W.dim
+    attempts_per_step = n_chains * V * S
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        ctx.run_sweeps(S, count_roundtrips=True)
+        ctx.update_weights()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    rt0 = total_rt(ctx)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # dominant kernel alone: one sweeps launch per step, timed with its own events
+    k_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))                       # evict L2 between steps
+                starts[k].record(stream)
+                k_starts[k].record(stream)
+                ctx.run_sweeps(S, count_roundtrips=True)
+                k_ends[k].record(stream)
+                ctx.update_weights()
+                ends[k].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [s.elapsed_time(e) for s, e in zip(k_starts, k_ends)]
+    t_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+        torch.distributed.barrier()
+    rts = total_rt(ctx) - rt0
+    value = world * attempts_per_step * args.steps / (t_ms * 1e6)
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    achieved_ops = attempts_per_step * ALG_OPS_PER_ATTEMPT / kern_avg_s
+    props = torch.cuda.get_device_properties(0)
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 4 * 32 * sm_max * 1e6   # lane-instr/s issue limit
+
+    # end to end through the C ABI with host buffers (weights in, histograms/weights/rt out)
+    rows = max(d["b_top"] for d in ctx.describe()) + 1
+    lnW_host = ctx.get_weights(rows=rows)
+    e2e_ms = []
+    for k in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            ctx.set_weights(0, lnW_host)
+            ctx.run_sweeps(S, count_roundtrips=True)
+            hist = ctx.histograms(rows=rows)
+            ctx.update_weights()
+            lnW_host = ctx.get_weights(rows=rows)
+            rt = ctx.roundtrips()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = lnW_host.nbytes
+    d2h = hist.nbytes + lnW_host.nbytes + len(rt) * 32
+
+    plain = None
+    if not args.no_plain and rank == 0:
+        plain = plain_form(eamc, stream, S=200)
+
+    return {
+        "value": value, "t_ms": t_ms, "step_ms": step_ms, "kern_ms": kern_ms, "wall": wall,
+        "rts": rts, "attempts_per_step": attempts_per_step, "n_chains": n_chains,
+        "achieved_ops": achieved_ops, "alu_peak": alu_peak, "clocks": clk.summary(),
+        "e2e_ms": statistics.median(e2e_ms), "h2d": h2d, "d2h": d2h, "plain": plain,
+        "sm_count": props.multi_processor_count,
+    }
+
+
+def plain_form(eamc, stream, S: int):
+    """One realization per launch: the same kernel with a single chain in the context."""
+    import torch
+    W = HEADLINE
+    ctx = eamc.Context(seed=W.seed, device=0, stream=stream.cuda_stream)
+    ctx.init_disorder(W.dim, W.L, 1, rid0=0)
+    ctx.set_ensemble(0, 1, eamc.EA_POWERLAW, W.alpha, W.pole)
+    with torch.cuda.stream(stream):
+        ctx.run_sweeps(S)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        ctx.run_sweeps(S)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"value": W.L ** W.dim * S / (ms * 1e6), "unit": UNIT,
+            "what": f"one realization per launch, {S} sweeps, L={W.L}"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    W = HEADLINE
+    config = {"workload": W.name, "L": W.L, "realizations_per_gpu": W.n_real,
+              "chains_per_gpu": 2 * W.n_real, "ensembles": ["flat", "power-law(alpha=-3.6, dE=96)"],
+              "sweeps_per_step": args.sweeps_per_step,
+              "step": "sweeps with measurement + one weight-iteration update",
+              "l2": "flushed between steps (256 MB write)",
+              "parallelism": f"independent realizations, {world} GPU(s)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        per = max(4.0, 60.0 / max(1, args.steps + args.warmup))
+        base = None
+        for k in range(args.warmup + args.steps):
+            base = oracle_sample(target_s=min(per, 20.0))
+            if k >= args.warmup:
+                steps.append(base)
+        val = statistics.mean(s["value"] for s in steps)
+        wall = sum(s["wall_s"] for s in steps)
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, len(steps)),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic (seeded +-J disorder)", "config": config, "impl": "reference",
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                                 "sample": base["sample"]},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()      # spawn pool before the first CUDA call
+    r = run_gpu(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    attempts_e2e = r["attempts_per_step"] * world
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["t_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded +-J disorder, random initial spins)", "config": config,
+        "round_trips_per_s": world * r["rts"] / (r["t_ms"] / 1e3),
+        "plain_form": r["plain"],
+        "e2e": {"value": attempts_e2e / (r["e2e_ms"] * 1e6), "unit": UNIT,
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "achieved": r["achieved_ops"] / 1e12,
+                     "peak": r["alu_peak"] / 1e12, "unit": "Tops/s",
+                     "frac": r["achieved_ops"] / r["alu_peak"], "traffic": None,
+                     "kernel": "muca_sweep_kernel<3>",
+                     "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
+                     "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock"},
+        "clocks": r["clocks"],
+        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
