@@ -22,9 +22,10 @@
  *     thr[b*8 + n] is used for a move from bin b at a site with n unsatisfied bonds
  *     (the move changes E by 2*(2*dim) - 4n); EA_ALWAYS accepts unconditionally, any
  *     other value accepts iff the move's 32-bit random word r < thr.
- *   - Random words come from Philox4x32-10 keyed by the context seed; counters are
- *     (i>>2, sweep t, rid, stream<<8) for MUCA updates, so a chain's trajectory does not
- *     depend on which other chains share the batch.
+ *   - Random words come from Philox4x32-10 keyed by the context seed.  The MUCA update of
+ *     site (x, row) in sweep t uses word x&3 of counter (4*row + x/4, t, rid, stream<<8),
+ *     row = y (+ L*z), so a chain's trajectory does not depend on which other chains share
+ *     the batch.
  *   - All pointers in this header are HOST pointers to caller-owned buffers unless stated
  *     otherwise; inputs are copied before the call returns, outputs are written before it
  *     returns.  Device state lives in the context until ea_destroy.
@@ -89,7 +90,7 @@ int ea_create(ea_ctx **out, int device, void *cuda_stream, uint64_t seed);
 void ea_destroy(ea_ctx *ctx);
 
 /* a1 -- disorder and initial state (Sec. II: 3V couplings J = +-1 with p = 1/2, quenched).
- * Appends n chains of linear size L (dim 2 or 3, 3 <= L <= 16) for realizations
+ * Appends n chains of linear size L (dim 2 or 3, 3 <= L <= 12) for realizations
  * rid0, rid0+1, ... with random stream `stream`.  couplings_or_null: NULL to draw the
  * couplings from the seed, else int8[n][dim*V] of +-1.  spins_or_null: NULL for random
  * initial spins, else int8[n][V] of +-1.  Each chain then descends deterministically

@@ -23,7 +23,8 @@
  *   RNG          Philox4x32-10, key = (seed lo, seed hi).  Counter words:
  *                  disorder      (j>>2, 0, rid, 3)            word j&3, j = bond index
  *                  initial spins (i>>2, 0, rid, 2 | stream<<8) word i&3
- *                  MUCA update   (i>>2, t, rid, 0 | stream<<8) word i&3
+ *                  MUCA update   (4*row + x/4, t, rid, 0 | stream<<8) word x&3, where
+ *                                row = y (+ L z) is the site's lattice row along x
  *                  PT update     (8*i + m/4, t, rid>>5, 4 | slot<<8) word m&3,
  *                                32 words whose bit (rid&31) gives bit 31-m of r
  *                  PT swap       (k, t, rid, 1) word 0
@@ -194,8 +195,9 @@ int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
     for (uint64_t s = 0; s < n_sweeps; ++s) {
         uint64_t t = t0 + s;
         for (int i = 0; i < V; ++i) {
-            uint32_t r = rand_word(seed, (uint32_t)(i >> 2), (uint32_t)t, rid,
-                                   0u | (stream << 8), i & 3);
+            int x = i % L, row = i / L;            /* row = y (+ L z) */
+            uint32_t r = rand_word(seed, (uint32_t)(4 * row + (x >> 2)), (uint32_t)t, rid,
+                                   0u | (stream << 8), x & 3);
             int h = local_field(dim, L, J, S, i);
             int n_unsat = (z - S[i] * h) / 2;        /* S_i h_i = #sat - #unsat */
             int dE = 2 * S[i] * h;                    /* = 2z - 4 n_unsat */

@@ -277,7 +277,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
                                 const int8_t *couplings, const int8_t *spins_in, int *first_chain) {
     if (!ctx) return fail(EA_EINVAL, "null context");
     if (dim != 2 && dim != 3) return fail(EA_EINVAL, "dim must be 2 or 3 (got %d)", dim);
-    if (L < 3 || L > 16) return fail(EA_EINVAL, "L must be in [3, 16] (got %d)", L);
+    if (L < 3 || L > 12) return fail(EA_EINVAL, "L must be in [3, 12] (got %d)", L);
     if (n <= 0) return fail(EA_EINVAL, "n must be positive (got %d)", n);
     if (stream >= (1u << 24)) return fail(EA_EINVAL, "stream must be < 2^24");
     if (ctx->dim && ctx->dim != dim) return fail(EA_EINVAL, "a context holds a single dim");
@@ -360,6 +360,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     ctx->bond_used = bond_used;
     ctx->w_used = w_used;
     ctx->max_V = std::max(ctx->max_V, V);
+    ctx->sweep_smem = std::max(ctx->sweep_smem, sweep_smem_bytes(dim, L));
     for (int k = 0; k < n; ++k) {
         const int slot = (tile0 + k / kTile) * kTile + k % kTile;
         ctx->chain_slot.push_back(slot);
@@ -516,9 +517,9 @@ extern "C" int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtr
     if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains: call ea_init_disorder first");
     if (n_sweeps > (1ull << 32) || ctx->max_t_host + n_sweeps > (1ull << 32))
         return fail(EA_EINVAL, "sweep counter would exceed 2^32");
-    EA_CUDA(launch_sweeps(ctx->d_tiles, (int)ctx->tiles.size(), ctx->dim, ctx->max_V, ctx->d_slots,
-                          ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, n_sweeps, ctx->key,
-                          count_roundtrips, ctx->stream));
+    EA_CUDA(launch_sweeps(ctx->d_tiles, nullptr, (int)ctx->tiles.size(), ctx->dim, ctx->sweep_smem,
+                          ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, n_sweeps,
+                          ctx->key, count_roundtrips, ctx->stream));
     ctx->max_t_host += n_sweeps;
     return EA_OK;
 }

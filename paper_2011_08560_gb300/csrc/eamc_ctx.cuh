@@ -16,6 +16,7 @@ struct ea_ctx {
     eamc::PhiloxKey key{0, 0};
     int dim = 0;
     int max_V = 0;
+    size_t sweep_smem = 0;    // dynamic shared memory of the sweep launch (largest tile)
     uint64_t max_t_host = 0;  // upper bound of every chain's sweep counter
 
     // host mirrors

@@ -1,18 +1,13 @@
 // muca_kernels.cu -- sm_103a kernels of the multicanonical (MUCA) hot path.
 //
 //   init_kernel            a1: disorder, initial spins, energy, descent to E <= E_top
-//   muca_sweep_kernel      a2+a3: sequential single-spin-flip generalized Metropolis
-//                          (Eq. "muca") with histogram, lowest energy and round trips
+//   (the sweep kernel itself, a2+a3, is in muca_sweep.cu)
 //   update_weights_kernel  a4: W <- W P_SH / H (Sec. II iterative procedure), FP64
 //   quantize_kernel        a4: ln W -> u32 acceptance thresholds
 //   build_ensemble_kernel  a5: flat / power-law / 1/k / canonical weights from ln Omega
 //
-// One warp = one tile of 32 chains of equal (dim, L).  The lattice of the tile is
-// multi-spin coded (bit `lane` of each word is chain `lane`) and staged in shared memory,
-// so every spin / bond read is a warp-broadcast LDS; each lane then works on its own chain:
-// its own Philox stream, energy bin, threshold row and round-trip state.  MUCA is
-// sequential within a chain because W depends on the total energy, so all parallelism
-// comes from the chains.
+// One warp = one tile of 32 chains of equal (dim, L); in global memory the tile's lattice is
+// multi-spin coded (bit `lane` of each word is chain `lane`).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -24,34 +19,6 @@ namespace eamc {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-
-__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
-    return (a & b) | (a & c) | (b & c);
-}
-
-// bit-sliced number of set bits among the 2*DIM "unsatisfied" words: p0 + 2 p1 + 4 p2
-template <int DIM>
-__device__ __forceinline__ void count_unsat(const uint32_t *u, uint32_t &p0, uint32_t &p1,
-                                            uint32_t &p2) {
-    if constexpr (DIM == 3) {
-        const uint32_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
-        const uint32_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
-        p0 = s1 ^ s2;
-        const uint32_t c3 = s1 & s2;
-        p1 = c1 ^ c2 ^ c3;
-        p2 = maj3(c1, c2, c3);
-    } else {
-        const uint32_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
-        p0 = s1 ^ u[3];
-        const uint32_t c2 = s1 & u[3];
-        p1 = c1 ^ c2;
-        p2 = c1 & c2;
-    }
-}
-
-__device__ __forceinline__ int lane_count(uint32_t p0, uint32_t p1, uint32_t p2, int lane) {
-    return (int)(((p0 >> lane) & 1u) | (((p1 >> lane) & 1u) << 1) | (((p2 >> lane) & 1u) << 2));
-}
 
 // neighbour of site i along d (0..DIM-1) with sign +-1, from coordinates
 template <int DIM>
@@ -177,115 +144,6 @@ init_kernel(const TileDesc *__restrict__ tiles, int tile0, SlotState *__restrict
     ss.requeue = 0;
     ss.active = ok ? 1 : 0;
     slots[tile * kTile + lane] = ss;
-}
-
-// ------------------------------------------------------------------------------ a2+a3
-// smem: spins (V words, padded to 16 B) then per site a bond record: DIM=3 ->
-// [J+x, J+y, J+z, 0, J-x, J-y, J-z, 0], DIM=2 -> [J+x, J+y, J-x, J-y]; J-d is the bond to
-// the neighbour at -e_d.  The records duplicate each bond so one site needs two LDS.128.
-template <int DIM>
-__global__ void __launch_bounds__(32)
-muca_sweep_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
-                  uint32_t *__restrict__ spins, const uint32_t *__restrict__ bonds,
-                  const uint32_t *__restrict__ thr, uint32_t *__restrict__ hist,
-                  uint64_t n_sweeps, PhiloxKey key, int count_rt) {
-    constexpr int BW = (DIM == 3) ? 8 : 4;
-    extern __shared__ __align__(16) uint32_t smem[];
-    const TileDesc td = tiles[blockIdx.x];
-    const int lane = threadIdx.x;
-    const int L = td.L, V = td.V, LL = L * L;
-    uint32_t *sp = smem;
-    uint32_t *bd = smem + ((V + 3) & ~3);
-    for (int k = lane; k < V; k += 32) sp[k] = spins[td.spin_off + k];
-    for (int i = lane; i < V; i += 32) {
-        const uint32_t *g = bonds + td.bond_off;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            bd[i * BW + d] = g[i * DIM + d];
-            bd[i * BW + BW / 2 + d] = g[nbr<DIM>(i, L, d, -1) * DIM + d];
-        }
-        if (DIM == 3) { bd[i * BW + 3] = 0u; bd[i * BW + 7] = 0u; }
-    }
-    __syncwarp();
-
-    const int slot = blockIdx.x * kTile + lane;
-    SlotState ss = slots[slot];
-    const bool active = ss.active != 0;
-    const uint32_t *thr_l = thr + (td.w_base + (uint64_t)lane * td.B) * 8;
-    uint32_t *hist_l = hist + td.w_base + (uint64_t)lane * td.B;
-    int b = ss.b, bmin = ss.b_min, phase = ss.phase, nrt = ss.n_rt;
-    const int btop = ss.b_top, bg = ss.b_g;
-    int64_t tf = ss.t_first, tl = ss.t_last;
-    const uint64_t t0 = ss.t;
-    const uint32_t c2 = ss.rid, c3 = ss.stream << 8;
-
-    for (uint64_t s = 0; s < n_sweeps; ++s) {
-        const uint32_t tt = (uint32_t)(t0 + s);
-        int x = 0, y = 0, z = 0;
-        for (int i0 = 0; i0 < V; i0 += 4) {
-            const uint4 r4 = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), tt, c2, c3), key);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = i0 + j;
-                if (i < V) {
-                    const uint32_t r = uint4_get(r4, j);
-                    const int xm = (x == 0) ? i + (L - 1) : i - 1;
-                    const int xp = (x == L - 1) ? i - (L - 1) : i + 1;
-                    const int ym = (y == 0) ? i + (LL - L) : i - L;
-                    const int yp = (y == L - 1) ? i - (LL - L) : i + L;
-                    const uint32_t si = sp[i];
-                    const uint4 bp = *reinterpret_cast<const uint4 *>(bd + i * BW);
-                    uint32_t u[2 * DIM];
-                    if constexpr (DIM == 3) {
-                        const int zm = (z == 0) ? i + (V - LL) : i - LL;
-                        const int zp = (z == L - 1) ? i - (V - LL) : i + LL;
-                        const uint4 bm = *reinterpret_cast<const uint4 *>(bd + i * BW + 4);
-                        u[0] = si ^ sp[xp] ^ bp.x;
-                        u[1] = si ^ sp[yp] ^ bp.y;
-                        u[2] = si ^ sp[zp] ^ bp.z;
-                        u[3] = si ^ sp[xm] ^ bm.x;
-                        u[4] = si ^ sp[ym] ^ bm.y;
-                        u[5] = si ^ sp[zm] ^ bm.z;
-                    } else {
-                        u[0] = si ^ sp[xp] ^ bp.x;
-                        u[1] = si ^ sp[yp] ^ bp.y;
-                        u[2] = si ^ sp[xm] ^ bp.z;
-                        u[3] = si ^ sp[ym] ^ bp.w;
-                    }
-                    uint32_t p0, p1, p2;
-                    count_unsat<DIM>(u, p0, p1, p2);
-                    const int n = lane_count(p0, p1, p2, lane);
-                    const uint32_t th = __ldg(thr_l + b * 8 + n);
-                    const bool acc = active && (th == kAlways || r < th);
-                    const uint32_t m = __ballot_sync(kFull, acc);
-                    sp[i] = si ^ m;
-                    if (acc) b += DIM - n;
-                    bmin = min(bmin, b);
-                    if (count_rt && active) {
-                        const bool trig = (phase == 1) ? (b <= bg) : (b >= btop);
-                        if (trig) {
-                            if (phase == 0) { tf = (int64_t)(t0 + s); phase = 1; }
-                            else if (phase == 1) { phase = 2; }
-                            else { nrt += 1; tl = (int64_t)(t0 + s); phase = 1; }
-                        }
-                    }
-                }
-                if (++x == L) { x = 0; if (++y == L) { y = 0; ++z; } }
-            }
-        }
-        if (active) hist_l[b] += 1u;
-    }
-    __syncwarp();
-    for (int k = lane; k < V; k += 32) spins[td.spin_off + k] = sp[k];
-    ss.b = b;
-    ss.b_min = bmin;
-    ss.phase = phase;
-    ss.n_rt = nrt;
-    ss.t_first = tf;
-    ss.t_last = tl;
-    ss.t = t0 + n_sweeps;
-    if (count_rt && active && energy_of_bin(td.dim * V, ss.parity, bmin) < ss.e_g) ss.requeue = 1;
-    slots[slot] = ss;
 }
 
 // ------------------------------------------------------------------------------ a4
@@ -457,34 +315,6 @@ cudaError_t launch_init(const TileDesc *d_tiles, int tile0, int n_tiles, int dim
     else
         init_kernel<2><<<n_tiles, 32, 0, st>>>(d_tiles, tile0, d_slots, d_spins, d_bonds, d_J,
                                                d_S, in_row0, key, d_err);
-    return cudaGetLastError();
-}
-
-static size_t sweep_smem_bytes(int dim, int V) {
-    const int bw = dim == 3 ? 8 : 4;
-    return (size_t)(((V + 3) & ~3) + bw * V) * sizeof(uint32_t);
-}
-
-cudaError_t launch_sweeps(const TileDesc *d_tiles, int n_tiles, int dim, int max_V,
-                          SlotState *d_slots, uint32_t *d_spins, const uint32_t *d_bonds,
-                          const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
-                          PhiloxKey key, int count_rt, cudaStream_t st) {
-    if (n_tiles <= 0 || n_sweeps == 0) return cudaSuccess;
-    const size_t smem = sweep_smem_bytes(dim, max_V);
-    cudaError_t e;
-    if (dim == 3) {
-        e = cudaFuncSetAttribute(muca_sweep_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        muca_sweep_kernel<3><<<n_tiles, 32, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr,
-                                                        d_hist, n_sweeps, key, count_rt);
-    } else {
-        e = cudaFuncSetAttribute(muca_sweep_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        muca_sweep_kernel<2><<<n_tiles, 32, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr,
-                                                        d_hist, n_sweeps, key, count_rt);
-    }
     return cudaGetLastError();
 }
 
