@@ -64,6 +64,32 @@ int grow(T **ptr, size_t *cap, size_t used, size_t need, cudaStream_t st) {
     return EA_OK;
 }
 
+// Threshold tables get kThrPad zero elements before and after the used range: the sweep
+// kernel may read (never use) a row one move beyond a chain's table.
+constexpr size_t kThrPad = 64;
+
+int grow_thr(ea_ctx *ctx, size_t need) {
+    if (need <= ctx->thr_cap) return EA_OK;
+    size_t ncap = std::max(need, ctx->thr_cap * 2);
+    uint32_t *raw = nullptr;
+    if (cudaMalloc(&raw, (ncap + 2 * kThrPad) * sizeof(uint32_t)) != cudaSuccess)
+        return fail(EA_ENOMEM, "device allocation of the threshold tables failed");
+    cudaMemsetAsync(raw, 0, (ncap + 2 * kThrPad) * sizeof(uint32_t), ctx->stream);
+    uint32_t *np = raw + kThrPad;
+    if (ctx->d_thr && ctx->w_used) {
+        cudaError_t e = cudaMemcpyAsync(np, ctx->d_thr, ctx->w_used * 8 * sizeof(uint32_t),
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) { cudaFree(raw); return cuda_fail(e, "grow copy"); }
+    }
+    if (ctx->d_thr) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_thr - kThrPad);
+    }
+    ctx->d_thr = np;
+    ctx->thr_cap = ncap;
+    return EA_OK;
+}
+
 // rows of per-chain tables <-> a dense [n][stride] staging array
 template <class T>
 __global__ void gather_rows(const T *__restrict__ table, const uint64_t *__restrict__ off,
@@ -264,8 +290,9 @@ extern "C" void ea_destroy(ea_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     pt_release(ctx);
-    void *ptrs[] = {ctx->d_tiles, ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_lnW,
-                    ctx->d_hist,  ctx->d_thr,   ctx->d_scratch, ctx->d_err, ctx->d_Jin};
+    void *ptrs[] = {ctx->d_tiles, ctx->d_slots, ctx->d_spins,   ctx->d_bonds, ctx->d_lnW,
+                    ctx->d_hist,  ctx->d_thr ? ctx->d_thr - kThrPad : nullptr,
+                    ctx->d_scratch, ctx->d_err, ctx->d_Jin};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -313,7 +340,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
         (rc = grow(&ctx->d_bonds, &ctx->bonds_cap, ctx->bond_used, bond_used, ctx->stream)) ||
         (rc = grow(&ctx->d_lnW, &ctx->lnW_cap, ctx->w_used, w_used, ctx->stream)) ||
         (rc = grow(&ctx->d_hist, &ctx->hist_cap, ctx->w_used, w_used, ctx->stream)) ||
-        (rc = grow(&ctx->d_thr, &ctx->thr_cap, ctx->w_used * 8, w_used * 8, ctx->stream)))
+        (rc = grow_thr(ctx, w_used * 8)))
         return rc;
     EA_CUDA(cudaMemcpyAsync(ctx->d_tiles + tile0, nt.data(), new_tiles * sizeof(TileDesc),
                             cudaMemcpyHostToDevice, ctx->stream));

@@ -67,10 +67,13 @@ struct Geo {
     static constexpr int B = ((DIM * V) / 2 >> 1) + 1;       // table rows per chain
     static constexpr int NG = (L + 3) / 4;                   // Philox calls per row
     static constexpr int FIELDS = DIM + 2;                   // S, Jx, Jx(shifted), Jy, (Jz)
+    static constexpr int SUMQ = sizeof(T) == 4 ? 1 : 2;      // uint4 slots for sA,sB,R,JYm
+    static constexpr int HQ = SUMQ + NG;                     // uint4 slots per lane per row
     static constexpr size_t LATTICE_BYTES = (size_t)FIELDS * NR * 32 * sizeof(T);
-    static constexpr size_t THR_BYTES = (size_t)B * 8 * 32 * sizeof(uint32_t);
-    static constexpr bool SMEM_THR = LATTICE_BYTES + THR_BYTES <= 200 * 1024;
-    static constexpr size_t SMEM = LATTICE_BYTES + (SMEM_THR ? THR_BYTES : 0);
+    static constexpr size_t HAND_BYTES = (size_t)2 * HQ * 32 * 16;
+    static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * 32 * sizeof(uint32_t);
+    static constexpr bool SMEM_THR = LATTICE_BYTES + HAND_BYTES + THR_BYTES <= 200 * 1024;
+    static constexpr size_t SMEM = LATTICE_BYTES + HAND_BYTES + (SMEM_THR ? THR_BYTES : 0);
 };
 
 template <bool SMEM>
@@ -79,6 +82,33 @@ __device__ __forceinline__ uint32_t load_thr(const uint32_t *p) {
     else return __ldg(p);
 }
 
+template <class T>
+__device__ __forceinline__ void put4(uint4 *slots, int q, int lane, T a, T b, T c, T d) {
+    if constexpr (sizeof(T) == 4) {
+        slots[q * 32 + lane] = make_uint4(a, b, c, d);
+    } else {
+        slots[q * 32 + lane] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+        slots[(q + 1) * 32 + lane] = make_uint4((uint32_t)c, (uint32_t)(c >> 32), (uint32_t)d, (uint32_t)(d >> 32));
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void get4(const uint4 *slots, int q, int lane, T &a, T &b, T &c, T &d) {
+    if constexpr (sizeof(T) == 4) {
+        const uint4 v = slots[q * 32 + lane];
+        a = v.x; b = v.y; c = v.z; d = v.w;
+    } else {
+        const uint4 v = slots[q * 32 + lane], w = slots[(q + 1) * 32 + lane];
+        a = ((T)v.y << 32) | v.x; b = ((T)v.w << 32) | v.z;
+        c = ((T)w.y << 32) | w.x; d = ((T)w.w << 32) | w.z;
+    }
+}
+
+// Two warps per tile.  Warp 1 (producer) works one row ahead of warp 0 (consumer): it draws
+// the row's random words and sums, per site, the unsatisfied-bond indicators of the bonds that
+// cannot change while the consumer sweeps that row.  The consumer adds the bond to the row
+// it has just finished (-y) and runs the sequential accept / reject chain.  A block barrier
+// per row hands over a double-buffered record.
 template <int DIM, int L>
 __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotState *__restrict__ slots,
                                            uint32_t *__restrict__ spins,
@@ -91,18 +121,21 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     constexpr int NR = G::NR;
     constexpr T NIB = nib_mask<T, L>();
     constexpr T LASTNIB = T(1) << (4 * (L - 1));
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x >= 32;
 
-    // ---- stage this lane's lattice as nibble-packed row words
+    // ---- stage the lattice as nibble-packed row words, lane-interleaved: word k of lane l
+    //      at [k*32 + l].  Nibble x of a row word is site x of that row.
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Rs = sm;                  // spins, nibble x = 1 if S = -1
-    T *JXs = sm + NR * 32;       // nibble x: bond (x, x+1) has J = -1
-    T *JXms = sm + 2 * NR * 32;  // nibble x: bond (x-1, x) has J = -1
-    T *JYs = sm + 3 * NR * 32;   // nibble x: bond (x,y)-(x,y+1)
-    T *JZs = sm + 4 * NR * 32;   // nibble x: bond (x,y,z)-(x,y,z+1)   (DIM == 3)
+    T *Rs = sm;                  // spins, nibble = 1 if S = -1
+    T *JXs = sm + NR * 32;       // bond (x, x+1) has J = -1
+    T *JXms = sm + 2 * NR * 32;  // bond (x-1, x) has J = -1
+    T *JYs = sm + 3 * NR * 32;   // bond (x,y)-(x,y+1)
+    T *JZs = sm + 4 * NR * 32;   // bond (x,y,z)-(x,y,z+1)   (DIM == 3)
+    uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
     const uint32_t *gsp = spins + td.spin_off;
     const uint32_t *gbd = bonds + td.bond_off;
-    for (int row = 0; row < NR; ++row) {
+    for (int row = producer ? 1 : 0; row < NR; row += 2) {
         T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
         for (int x = 0; x < L; ++x) {
@@ -123,108 +156,174 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     SlotState ss = slots[slot];
     const bool active = ss.active != 0;
     const uint64_t lrow = td.w_base + (uint64_t)lane * G::B;
-    // element (b, n) of this lane's table at tab[b * RS + n * NS]
-    constexpr int NS = G::SMEM_THR ? 32 : 1;
-    constexpr int RS = 8 * NS;
-    const uint32_t *tab;
+    // element (b, n) of this lane's table at byte offset b * RSB + n * NSB from `tab`; rows
+    // -DIM .. B-1+DIM are addressable (padding), so a speculative row one move away from a
+    // valid row never needs a clamp
+    constexpr int NSB = G::SMEM_THR ? 128 : 4;
+    constexpr int RSB = 8 * NSB;
+    const char *tab;
     if constexpr (G::SMEM_THR) {
-        uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES);
-        const uint4 *src = reinterpret_cast<const uint4 *>(thr + lrow * 8);
-        for (int b = 0; b < G::B; ++b) {
-            const uint4 a = src[2 * b], c = src[2 * b + 1];
-            uint32_t *d = TH + b * 256 + lane;
-            d[0] = a.x; d[32] = a.y; d[64] = a.z; d[96] = a.w;
-            d[128] = c.x; d[160] = c.y; d[192] = c.z; d[224] = c.w;
+        uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);
+        if (producer) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(thr + lrow * 8);
+            for (int b = 0; b < G::B; ++b) {
+                const uint4 a = src[2 * b], c = src[2 * b + 1];
+                uint32_t *d = TH + (b + DIM) * 256 + lane;
+                d[0] = a.x; d[32] = a.y; d[64] = a.z; d[96] = a.w;
+                d[128] = c.x; d[160] = c.y; d[192] = c.z; d[224] = c.w;
+            }
+            for (int k = 0; k < DIM * 8; ++k) {
+                TH[k * 32 + lane] = 0u;
+                TH[((G::B + DIM) * 8 + k) * 32 + lane] = 0u;
+            }
         }
-        tab = TH + lane;
+        tab = reinterpret_cast<const char *>(TH + DIM * 256 + lane);
     } else {
-        tab = thr + lrow * 8;
+        tab = reinterpret_cast<const char *>(thr + lrow * 8);
     }
-    __syncwarp();
-
-    int bmin = ss.b_min, phase = ss.phase, nrt = ss.n_rt;
-    const int btop = ss.b_top, bg = ss.b_g;
-    int64_t tf = ss.t_first, tl = ss.t_last;
     const uint64_t t0 = ss.t;
-    const uint32_t rid = ss.rid, c3 = ss.stream << 8;
-    uint32_t *hist_l = hist + lrow;
-    // outcome of the previous attempt, applied lazily: bin before it (bq), its unsatisfied
-    // count (pn) and whether it was accepted (pa)
-    int bq = ss.b, pn = DIM, pa = 0;
-    int bnow = ss.b;
+    const uint64_t total = n_sweeps * (uint64_t)NR;  // rows to sweep
 
-    for (uint64_t s = 0; s < n_sweeps; ++s) {
-        const uint64_t t = t0 + s;
-        const uint32_t tt = (uint32_t)t;
-        int y = 0, z = 0;
-        for (int row = 0; row < NR; ++row) {
-            const int rym = (y == 0) ? row + (L - 1) : row - 1;
-            const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
-            const T R = Rs[row * 32 + lane];
-            const T u_yp = R ^ Rs[ryp * 32 + lane] ^ JYs[row * 32 + lane];
-            const T u_ym = R ^ Rs[rym * 32 + lane] ^ JYs[rym * 32 + lane];
-            const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * 32 + lane];
-            const T u_xm = R ^ rot_prev<T, L>(R) ^ JXms[row * 32 + lane];
-            T sum = u_yp + u_ym + (u_xp & ~LASTNIB);
-            if constexpr (DIM == 3) {
-                const int rzm = (z == 0) ? row + (L - 1) * L : row - L;
-                const int rzp = (z == L - 1) ? row - (L - 1) * L : row + L;
-                sum += (R ^ Rs[rzp * 32 + lane] ^ JZs[row * 32 + lane]) +
-                       (R ^ Rs[rzm * 32 + lane] ^ JZs[rzm * 32 + lane]);
-            }
-            const T sumA = sum + u_xm;          // -x bond as before the row
-            const T sumB = sum + (u_xm ^ NIB);  // -x bond toggled by a flip of site x-1
-            uint4 rr[G::NG];
-#pragma unroll
-            for (int g = 0; g < G::NG; ++g)
-                rr[g] = philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, rid, c3), key);
-            T accN = 0;  // nibble x = 1 if this chain flipped site x of the row
-#pragma unroll
-            for (int x = 0; x < L; ++x) {
-                int nA = (int)((sumA >> (4 * x)) & 0xF);
-                int nB = (x == 0) ? nA : (int)((sumB >> (4 * x)) & 0xF);
-                if (x == L - 1) {  // bond to site 0 of the row, flipped at x = 0 or not
-                    const int w = (int)((u_xp >> (4 * (L - 1))) & 1u) ^ (int)(accN & 1u);
-                    nA += w;
-                    nB += w;
-                }
-                const int bA = bq;
-                const int bB = min(max(bq + DIM - pn, 0), G::B - 1);
-                const uint32_t thA = load_thr<G::SMEM_THR>(tab + bA * RS + nA * NS);
-                const uint32_t thB = load_thr<G::SMEM_THR>(tab + bB * RS + nB * NS);
-                const int n = pa ? nB : nA;
-                const uint32_t th = pa ? thB : thA;
-                const int bx = pa ? bB : bA;
-                const uint32_t r = uint4_get(rr[x >> 2], x & 3);
-                const bool acc = active && (th == kAlways || r < th);
-                accN |= T(acc ? 1u : 0u) << (4 * x);
-                bnow = acc ? bx + DIM - n : bx;
-                bmin = min(bmin, bnow);
-                if (count_rt && active) {
-                    const bool trig = (phase == 1) ? (bnow <= bg) : (bnow >= btop);
-                    if (trig) {
-                        if (phase == 0) { tf = (int64_t)t; phase = 1; }
-                        else if (phase == 1) { phase = 2; }
-                        else { nrt += 1; tl = (int64_t)t; phase = 1; }
-                    }
-                }
-                pa = acc ? 1 : 0;
-                pn = n;
-                bq = bx;
-            }
-            Rs[row * 32 + lane] = R ^ accN;
-            if (++y == L) { y = 0; ++z; }
-        }
-        if (active) hist_l[bnow] += 1u;
-    }
-    __syncwarp();
-    // spins back to the multi-spin-coded global layout
-    for (int row = 0; row < NR; ++row) {
+    // producer: record of row `row` (sweep index tt) into buffer `k`
+    auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
+        uint4 *buf = hand + k * G::HQ * 32;
+        const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
         const T R = Rs[row * 32 + lane];
+        const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * 32 + lane];
+        const T u_xm = R ^ rot_prev<T, L>(R) ^ JXms[row * 32 + lane];
+        T stable = (R ^ Rs[ryp * 32 + lane] ^ JYs[row * 32 + lane]) + (u_xp & ~LASTNIB);
+        if constexpr (DIM == 3) {
+            const int rzm = (z == 0) ? row + (L - 1) * L : row - L;
+            const int rzp = (z == L - 1) ? row - (L - 1) * L : row + L;
+            stable += (R ^ Rs[rzp * 32 + lane] ^ JZs[row * 32 + lane]) +
+                      (R ^ Rs[rzm * 32 + lane] ^ JZs[rzm * 32 + lane]);
+        }
+        // the -y row: the consumer's previous row (add later) unless (3D, y = 0), where it is
+        // the plane's last row, not yet swept
+        T jym = 0;
+        const int rym = (y == 0) ? row + (L - 1) : row - 1;
+        if (DIM == 3 && y == 0) stable += R ^ Rs[rym * 32 + lane] ^ JYs[rym * 32 + lane];
+        else jym = JYs[rym * 32 + lane];
+        const T sA = stable + u_xm;
+        // nibble 0 of sB is never used (site 0 has no dynamic -x bond): its bit 3 carries the
+        // stale wrap bond of site L-1
+        const T wbit = (u_xp >> (4 * (L - 1))) & T(1);
+        const T sB = ((stable + (u_xm ^ NIB)) & ~T(0xF)) | (wbit << 3);
+        put4<T>(buf, 0, lane, sA, sB, R, jym);
+        const uint32_t c3 = ss.stream << 8;
+#pragma unroll
+        for (int g = 0; g < G::NG; ++g)
+            buf[(G::SUMQ + g) * 32 + lane] =
+                philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
+    };
+
+    __syncthreads();
+    if (producer) {
+        if (total > 0) produce(0, 0, 0, (uint32_t)t0, 0);
+        int row = 0, y = 0, z = 0;
+        uint64_t s = 0;
+        for (uint64_t k = 0; k < total; ++k) {
+            if (++y == L) { y = 0; ++z; }
+            if (++row == NR) { row = 0; y = 0; z = 0; ++s; }
+            // barrier k: record k is complete and the consumer has finished with record k-1,
+            // whose buffer ((k+1)&1) is refilled with record k+1
+            __syncthreads();
+            if (k + 1 < total) produce(row, y, z, (uint32_t)(t0 + s), (int)((k + 1) & 1));
+        }
+        return;  // both warps pass exactly 1 + total block barriers
+    }
+
+    // ---- consumer
+    int phase = ss.phase, nrt = ss.n_rt;
+    int64_t tf = ss.t_first, tl = ss.t_last;
+    uint32_t *hist_l = hist + lrow;
+    const int topB = ss.b_top * RSB, botB = ss.b_g * RSB;
+    int pmin = ss.b_min * RSB;
+    // the previous attempt, applied lazily: row it was evaluated at (rq), row delta if it was
+    // accepted (dq) and whether it was (pa)
+    int rq = ss.b * RSB, dq = 0, pa = 0;
+    int pnow = rq;
+    T Rprev = Rs[(NR - 1) * 32 + lane];
+    int row = 0, y = 0;
+    uint64_t s = 0;
+    for (uint64_t k = 0; k < total; ++k) {
+        __syncthreads();                           // record k is complete
+        const uint4 *buf = hand + (int)(k & 1) * G::HQ * 32;
+        T sA, sB, R, jym;
+        get4<T>(buf, 0, lane, sA, sB, R, jym);
+        uint4 rr[G::NG];
+#pragma unroll
+        for (int g = 0; g < G::NG; ++g) rr[g] = buf[(G::SUMQ + g) * 32 + lane];
+        if (DIM == 2 || y > 0) {
+            const T uym = R ^ Rprev ^ jym;
+            sA += uym;
+            sB += uym;
+        }
+        const int wbit = (int)((sB >> 3) & 1u);
+        T accN = 0;   // nibble x = 1 if this chain flipped site x of the row
+        int prow[L];  // row offset after each attempt (measurement at the row end)
 #pragma unroll
         for (int x = 0; x < L; ++x) {
-            const uint32_t m = __ballot_sync(kFull, ((R >> (4 * x)) & 1u) != 0);
-            if (lane == 0) spins[td.spin_off + row * L + x] = m;
+            int nA = (int)((sA >> (4 * x)) & 0xF);
+            int nB = (x == 0) ? nA : (int)((sB >> (4 * x)) & 0xF);
+            if (x == L - 1) {  // bond to site 0 of the row, flipped at x = 0 or not
+                const int w = wbit ^ (int)(accN & 1u);
+                nA += w;
+                nB += w;
+            }
+            const int rB = rq + dq;
+            const uint32_t thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + nA * NSB));
+            const uint32_t thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rB + nB * NSB));
+            const uint32_t th = pa ? thB : thA;
+            const int rx = pa ? rB : rq;
+            const int dx = (DIM - (pa ? nB : nA)) * RSB;
+            const uint32_t r = uint4_get(rr[x >> 2], x & 3);
+            const bool acc = active && (th == kAlways || r < th);
+            accN |= T(acc ? 1u : 0u) << (4 * x);
+            prow[x] = acc ? rx + dx : rx;
+            rq = rx;
+            dq = dx;
+            pa = acc ? 1 : 0;
+        }
+        const T Rfin = R ^ accN;
+        Rs[row * 32 + lane] = Rfin;
+        Rprev = Rfin;
+        // lowest energy and round trips: row minimum / maximum, exact replay only when the
+        // round-trip state can change within this row (rare)
+        int lo = prow[0], hi = prow[0];
+#pragma unroll
+        for (int x = 1; x < L; ++x) { lo = min(lo, prow[x]); hi = max(hi, prow[x]); }
+        pmin = min(pmin, lo);
+        pnow = prow[L - 1];
+        if (count_rt && active && ((phase == 1) ? (lo <= botB) : (hi >= topB))) {
+            const int64_t t = (int64_t)(t0 + s);
+#pragma unroll
+            for (int x = 0; x < L; ++x) {
+                const bool trig = (phase == 1) ? (prow[x] <= botB) : (prow[x] >= topB);
+                if (trig) {
+                    if (phase == 0) { tf = t; phase = 1; }
+                    else if (phase == 1) { phase = 2; }
+                    else { nrt += 1; tl = t; phase = 1; }
+                }
+            }
+        }
+        if (++y == L) y = 0;
+        if (++row == NR) {
+            row = 0;
+            y = 0;
+            ++s;
+            if (active) hist_l[pnow / RSB] += 1u;
+        }
+    }
+    __syncwarp();
+    const int bnow = pnow / RSB, bmin = pmin / RSB;
+    // spins back to the multi-spin-coded global layout
+    for (int r2 = 0; r2 < NR; ++r2) {
+        const T Rw = Rs[r2 * 32 + lane];
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            const uint32_t m = __ballot_sync(kFull, ((Rw >> (4 * x)) & 1u) != 0);
+            if (lane == 0) spins[td.spin_off + r2 * L + x] = m;
         }
     }
     ss.b = bnow;
@@ -238,9 +337,9 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     slots[slot] = ss;
 }
 
-// One warp (32 chains of one tile) per block; the tile's L selects the compiled body.
+// Two warps (consumer + producer) per tile of 32 chains; the tile's L selects the body.
 template <int DIM>
-__global__ void __launch_bounds__(32, 1)
+__global__ void __launch_bounds__(64, 1)
 muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ tile_list,
                   SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
                   const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
@@ -291,12 +390,12 @@ cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, i
     if (dim == 3) {
         e = cudaFuncSetAttribute(muca_sweep_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        muca_sweep_kernel<3><<<n_blocks, 32, smem, st>>>(d_tiles, d_tile_list, d_slots, d_spins, d_bonds,
+        muca_sweep_kernel<3><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, d_slots, d_spins, d_bonds,
                                                          d_thr, d_hist, n_sweeps, key, count_rt);
     } else {
         e = cudaFuncSetAttribute(muca_sweep_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        muca_sweep_kernel<2><<<n_blocks, 32, smem, st>>>(d_tiles, d_tile_list, d_slots, d_spins, d_bonds,
+        muca_sweep_kernel<2><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, d_slots, d_spins, d_bonds,
                                                          d_thr, d_hist, n_sweeps, key, count_rt);
     }
     return cudaGetLastError();
