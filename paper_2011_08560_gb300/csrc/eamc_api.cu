@@ -309,6 +309,11 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     if (stream >= (1u << 24)) return fail(EA_EINVAL, "stream must be < 2^24");
     if (ctx->dim && ctx->dim != dim) return fail(EA_EINVAL, "a context holds a single dim");
     EA_CUDA(cudaSetDevice(ctx->device));
+    int smem_optin = 0;
+    EA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (sweep_smem_bytes(dim, L) > (size_t)smem_optin)
+        return fail(EA_EINVAL, "L=%d needs %zu bytes of shared memory per block, the device allows %d", L,
+                    sweep_smem_bytes(dim, L), smem_optin);
     const int V = volume_of(dim, L), B = rows_of(dim, L);
     const int new_tiles = (n + kTile - 1) / kTile;
     const int tile0 = (int)ctx->tiles.size();

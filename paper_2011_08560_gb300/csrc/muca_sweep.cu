@@ -262,21 +262,27 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         const int wbit = (int)((sB >> 3) & 1u);
         T accN = 0;   // nibble x = 1 if this chain flipped site x of the row
         int prow[L];  // row offset after each attempt (measurement at the row end)
+        // software pipeline: iteration x resolves attempt x from acc(x-1), issues both
+        // candidate threshold loads of attempt x+1 (they need only acc(x-1)), then compares
+        int nA = (int)(sA & 0xF), nB = nA;
+        uint32_t thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + nA * NSB));
+        uint32_t thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + dq + nB * NSB));
 #pragma unroll
         for (int x = 0; x < L; ++x) {
-            int nA = (int)((sA >> (4 * x)) & 0xF);
-            int nB = (x == 0) ? nA : (int)((sB >> (4 * x)) & 0xF);
-            if (x == L - 1) {  // bond to site 0 of the row, flipped at x = 0 or not
-                const int w = wbit ^ (int)(accN & 1u);
-                nA += w;
-                nB += w;
-            }
-            const int rB = rq + dq;
-            const uint32_t thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + nA * NSB));
-            const uint32_t thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rB + nB * NSB));
             const uint32_t th = pa ? thB : thA;
-            const int rx = pa ? rB : rq;
+            const int rx = pa ? rq + dq : rq;
             const int dx = (DIM - (pa ? nB : nA)) * RSB;
+            if (x + 1 < L) {
+                nA = (int)((sA >> (4 * (x + 1))) & 0xF);
+                nB = (int)((sB >> (4 * (x + 1))) & 0xF);
+                if (x + 1 == L - 1) {  // bond to site 0 of the row, flipped at x = 0 or not
+                    const int w = wbit ^ (int)(accN & 1u);
+                    nA += w;
+                    nB += w;
+                }
+                thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + nA * NSB));
+                thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + dx + nB * NSB));
+            }
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
             const bool acc = active && (th == kAlways || r < th);
             accN |= T(acc ? 1u : 0u) << (4 * x);
