@@ -160,6 +160,52 @@ int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stride, int32_t
 /* Waits for all queued work of the context. */
 int ea_synchronize(ea_ctx *ctx);
 
+/* ------------------------------------------------------------------ parallel tempering
+ * a6 + a7 -- the paper's PT baseline (Sec. II, PT; Eq. "temperatureexchange"): M replicas of
+ * each realization, Metropolis at inverse temperatures beta_0 < ... < beta_{M-1} (slot 0
+ * hottest), exchanges between neighbouring slots.  A context holds one PT batch beside its
+ * MUCA chains. */
+
+/* Round-trip record of one PT replica (Sec. III, PT variant: between E_g and E_hot). */
+typedef struct {
+    int32_t n_rt, phase;
+    int64_t t_first, t_last;
+    int32_t e_min, pad;
+} ea_pt_stats;
+
+/* Sets up n_real realizations rid0 .. rid0+n_real-1 (rid0 a multiple of 32; realizations
+ * are packed 32 to a word) of an even-L lattice (4 <= L <= 12; the checkerboard needs even L)
+ * with M replicas (2 <= M <= 64) at host betas[M] (strictly increasing).  Couplings from the
+ * seed (as ea_init_disorder) or from couplings_or_null (int8[n_real][dim*V]); replica k of
+ * realization r starts from the random spins of stream k.  Metropolis thresholds
+ * floor(exp(-beta_k dE) 2^32) and exchange thresholds floor(exp(-(beta_{k+1}-beta_k) 4d) 2^32)
+ * are built on the device.  Replaces any previous PT batch of the context. */
+int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, int M, const double *betas,
+            const int8_t *couplings_or_null);
+
+/* Round-trip bounds per realization (host int32[n_real] each): bottom E_g, top E_hot. */
+int pt_set_rt_bounds(ea_ctx *ctx, const int32_t *e_g, const int32_t *e_hot);
+
+/* n_sweeps PT sweeps: per sweep, a checkerboard Metropolis sweep of every replica (sites with
+ * even coordinate sum first, each colour in lexicographic order), exchanges between slots
+ * (k, k+1) for k = t mod 2, t mod 2 + 2, ... (accepted if E_{k+1} >= E_k, else with
+ * probability exp((beta_{k+1}-beta_k)(E_{k+1}-E_k))), then, if count_roundtrips, one
+ * round-trip check per replica.  The random word of an uphill update of realization r at
+ * slot k, site i, sweep t has bit 31-m equal to bit r&31 of word m&3 of Philox counter
+ * (8i + m/4, t, r>>5, 4 | k<<8); the exchange (k, k+1) uses word 0 of (k, t, r, 1). */
+int pt_run(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
+
+/* State by slot: spins int8[n_real][M][V] (may be NULL), energies int32[n_real][M] (may be
+ * NULL), replica labels int32[n_real][M] (may be NULL; label = the slot a configuration
+ * started at), sweeps done (may be NULL). */
+int pt_get_state(ea_ctx *ctx, int8_t *spins, int32_t *E, int32_t *labels, uint64_t *t);
+
+/* Round-trip records by replica label, out[n_real][M]; reset restarts counting. */
+int pt_get_roundtrips(ea_ctx *ctx, ea_pt_stats *out, int reset);
+
+/* Accepted exchanges per slot pair (k, k+1), summed over realizations: uint64[M-1]. */
+int pt_get_swap_counts(ea_ctx *ctx, uint64_t *out);
+
 #ifdef __cplusplus
 }
 #endif

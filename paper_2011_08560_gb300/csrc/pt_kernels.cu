@@ -1,13 +1,671 @@
-// pt_kernels.cu -- parallel tempering (second kernel); filled in below.
+// pt_kernels.cu -- a6 + a7: parallel tempering (Sec. II, PT; Eq. "temperatureexchange").
+//
+// M replicas of every realization, one per temperature slot k (beta ascending with k, slot
+// 0 hottest).  Each sweep: a checkerboard Metropolis sweep of every slot (sites with even
+// coordinate sum first, then odd), then replica exchange between slots (k, k+1) for
+// k = t mod 2, t mod 2 + 2, ..., then one round-trip check per replica (Sec. III, PT variant:
+// between E_g and an energy typical of a high temperature, E_hot).
+//
+// Layout.  Realizations come in groups of 32 (realization id 32g + b is bit b); the
+// configuration at slot k of a group is one multi-spin-coded word per site, so all 32 bits
+// of a word share one temperature and one set of Metropolis thresholds.  Exchanges move
+// configurations (not temperatures) with masked XOR swaps of whole words.
+//
+// Acceptance.  For a site word the unsatisfied-bond count of every bit is a bit-sliced sum;
+// bits with dE <= 0 flip.  Each uphill bit b compares its 32-bit random number r_b with the
+// slot's threshold; r_b's bit 31-m is bit b of random word m (Philox4x32-10 of counter
+// (8i + m/4, t, g, 4 | k<<8), word m&3).  The comparison runs over bit planes from the most
+// significant one and stops when every uphill bit is decided, so a site word usually needs
+// a few random words rather than 32.
+//
+// Parallel work.  One thread-block cluster per group: CS CTAs, each owning M/CS consecutive
+// slots in shared memory.  Energies are recomputed after every sweep (bit-sliced counters,
+// warp bit-matrix transpose, popcount); exchanges between slots owned by different CTAs read
+// and write the neighbour CTA's shared memory (distributed shared memory) between cluster
+// barriers.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
 
 #include "eamc.h"
 #include "eamc_ctx.cuh"
+#include "eamc_internal.cuh"
 
-struct PtState {};
+namespace cg = cooperative_groups;
+using namespace eamc;
+
+struct PtRt {
+    int32_t phase, n_rt;
+    int64_t t_first, t_last;
+    int32_t e_min, pad;
+};
+
+struct PtState {
+    int dim = 0, L = 0, V = 0, nb = 0, M = 0, n_real = 0, n_groups = 0, cs = 1, dmax = 0;
+    uint32_t rid0 = 0;
+    uint64_t t = 0;
+    std::vector<double> betas;
+    uint32_t *d_spins = nullptr;   // [g][k][V]
+    uint32_t *d_bonds = nullptr;   // [g][nb]
+    int32_t *d_E = nullptr;        // [g][k][32]
+    int32_t *d_label = nullptr;    // [g][k][32]
+    PtRt *d_rt = nullptr;          // [g][label][32]
+    int32_t *d_bounds = nullptr;   // [g][32][2] (e_g, e_hot)
+    uint32_t *d_thr_k = nullptr;   // [M][8]
+    uint32_t *d_thr_pair = nullptr;  // [M-1][dmax+1]
+    unsigned long long *d_swaps = nullptr;  // [M-1]
+    int *d_err = nullptr;
+};
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
+    return (a & b) | (a & c) | (b & c);
+}
+
+// 32x32 bit-matrix transpose across a warp: afterwards lane t holds, in bit s, bit t of
+// what lane s held
+__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const uint32_t m = masks[s];
+        const uint32_t y = __shfl_xor_sync(kFull, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+template <int DIM, int L>
+struct PtGeo {
+    static constexpr int NR = DIM == 3 ? L * L : L;
+    static constexpr int V = NR * L;
+    static constexpr int NB = DIM * V;
+    static constexpr int HALF = V / 2;  // sites of one colour
+};
+
+// neighbour of site i along axis d (0 x, 1 y, 2 z), direction +1 / -1
+template <int DIM, int L>
+__device__ __forceinline__ int pt_nbr(int i, int d, int sgn) {
+    int x = i % L, y = (i / L) % L, z = DIM == 3 ? i / (L * L) : 0;
+    if (d == 0) x = (x + sgn + L) % L;
+    else if (d == 1) y = (y + sgn + L) % L;
+    else z = (z + sgn + L) % L;
+    return x + L * (y + L * z);
+}
+
+struct PtArgs {
+    uint32_t *spins;
+    const uint32_t *bonds;
+    int32_t *E;
+    int32_t *label;
+    PtRt *rt;
+    const int32_t *bounds;
+    const uint32_t *thr_k;
+    const uint32_t *thr_pair;
+    unsigned long long *swaps;
+    int M, spc, dmax, n_real;
+    uint32_t rid0;
+    uint64_t t0, n_sweeps;
+    int count_rt;
+    PhiloxKey key;
+};
+
+template <int DIM, int L>
+__global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
+    using G = PtGeo<DIM, L>;
+    constexpr int V = G::V, NB = G::NB, HALF = G::HALF;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int g = blockIdx.x / (int)cluster.num_blocks();
+    const int spc = a.spc, k0 = rank * spc, M = a.M;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *S = sm;                       // [spc][V]
+    uint32_t *J = S + spc * V;              // [NB], J[i*DIM + d]
+    int32_t *Es = (int32_t *)(J + NB);      // [spc][32]
+    int32_t *Ls = Es + spc * 32;            // [spc][32]
+    uint32_t *Th = (uint32_t *)(Ls + spc * 32);  // [spc][8]
+    uint32_t *Amask = Th + spc * 8;         // [spc] exchange masks of owned pairs
+
+    const uint32_t group_rid0 = a.rid0 + 32u * (uint32_t)g;
+    const int nvalid = min(32, a.n_real - 32 * g);
+    const uint32_t valid = nvalid >= 32 ? kFull : ((1u << nvalid) - 1u);
+
+    for (int k = tid; k < spc * V; k += blockDim.x)
+        S[k] = a.spins[((size_t)g * M + k0) * V + k];
+    for (int k = tid; k < NB; k += blockDim.x) J[k] = a.bonds[(size_t)g * NB + k];
+    for (int k = tid; k < spc * 32; k += blockDim.x) {
+        Es[k] = a.E[((size_t)g * M + k0) * 32 + k];
+        Ls[k] = a.label[((size_t)g * M + k0) * 32 + k];
+    }
+    for (int k = tid; k < spc * 8; k += blockDim.x) Th[k] = a.thr_k[k0 * 8 + k];
+    __syncthreads();
+    cluster.sync();
+
+    for (uint64_t s = 0; s < a.n_sweeps; ++s) {
+        const uint64_t t = a.t0 + s;
+        const uint32_t tt = (uint32_t)t;
+        // ---- checkerboard Metropolis sweep of every owned slot
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int item = tid; item < spc * HALF; item += blockDim.x) {
+                const int ks = item / HALF, j = item % HALF;
+                const int row = j / (L / 2), xh = j % (L / 2);
+                const int y = row % L, z = DIM == 3 ? row / L : 0;
+                const int x = 2 * xh + ((colour + y + z) & 1);
+                const int i = x + L * row;
+                uint32_t *Sk = S + ks * V;
+                const uint32_t si = Sk[i];
+                uint32_t u[2 * DIM];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const int jp = pt_nbr<DIM, L>(i, d, +1), jm = pt_nbr<DIM, L>(i, d, -1);
+                    u[2 * d] = si ^ Sk[jp] ^ J[i * DIM + d];
+                    u[2 * d + 1] = si ^ Sk[jm] ^ J[jm * DIM + d];
+                }
+                uint32_t n0, n1, n2;  // bit-sliced count of unsatisfied bonds
+                if constexpr (DIM == 3) {
+                    const uint32_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
+                    const uint32_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
+                    n0 = s1 ^ s2;
+                    const uint32_t c3 = s1 & s2;
+                    n1 = c1 ^ c2 ^ c3;
+                    n2 = maj3(c1, c2, c3);
+                } else {
+                    const uint32_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
+                    n0 = s1 ^ u[3];
+                    const uint32_t c2 = s1 & u[3];
+                    n1 = c1 ^ c2;
+                    n2 = c1 & c2;
+                }
+                // uphill classes: n < DIM unsatisfied bonds (dE = 2*(2*DIM) - 4n > 0)
+                uint32_t C[3];
+                C[0] = ~n2 & ~n1 & ~n0;
+                C[1] = ~n2 & ~n1 & n0;
+                C[2] = (DIM == 3) ? (~n2 & n1 & ~n0) : 0u;
+                const uint32_t up = C[0] | C[1] | C[2];
+                uint32_t acc = ~up;  // dE <= 0 always accepted
+                uint32_t und = up & valid;
+                const int k = k0 + ks;
+                const uint32_t T0 = Th[ks * 8 + 0], T1 = Th[ks * 8 + 1], T2 = Th[ks * 8 + 2];
+                uint4 w4 = make_uint4(0, 0, 0, 0);
+                for (int m = 0; m < 32 && und; ++m) {
+                    if ((m & 3) == 0)
+                        w4 = philox4x32_10(make_uint4((uint32_t)(8 * i + (m >> 2)), tt, (uint32_t)g + (a.rid0 >> 5),
+                                                      4u | ((uint32_t)k << 8)), a.key);
+                    const uint32_t R = uint4_get(w4, m & 3);
+                    const int sh = 31 - m;
+                    const uint32_t Tm = (C[0] & (0u - ((T0 >> sh) & 1u))) | (C[1] & (0u - ((T1 >> sh) & 1u))) |
+                                        (C[2] & (0u - ((T2 >> sh) & 1u)));
+                    acc |= und & ~R & Tm;   // r bit 0, threshold bit 1: r < threshold
+                    und &= ~(R ^ Tm);       // equal bits: still undecided
+                }
+                Sk[i] = si ^ (acc & valid);
+            }
+            __syncthreads();
+        }
+        // ---- energies of the owned slots: u_b = number of unsatisfied bonds of bit b
+        for (int k = tid; k < spc * 32; k += blockDim.x) Es[k] = 0;
+        __syncthreads();
+        for (int ks = 0; ks < spc; ++ks) {
+            const uint32_t *Sk = S + ks * V;
+            for (int base = warp * 32; base < V; base += nwarps * 32) {
+                const int i = base + lane;
+                uint32_t c0 = 0, c1 = 0;  // bit-sliced count (0..3) of this site's +d bonds
+                if (i < V) {
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        const uint32_t w = Sk[i] ^ Sk[pt_nbr<DIM, L>(i, d, +1)] ^ J[i * DIM + d];
+                        c1 ^= c0 & w;  // add one bit into the 2-bit counter (max 3)
+                        c0 ^= w;
+                    }
+                }
+                const uint32_t t0w = warp_transpose(c0, lane), t1w = warp_transpose(c1, lane);
+                const int cnt = __popc(t0w) + 2 * __popc(t1w);
+                atomicAdd(&Es[ks * 32 + lane], cnt);
+            }
+        }
+        __syncthreads();
+        for (int k = tid; k < spc * 32; k += blockDim.x) Es[k] = 2 * Es[k] - NB;
+        __syncthreads();
+        cluster.sync();  // every slot's energy is known
+        // ---- replica exchange between (k, k+1), k = t mod 2 (mod 2); the owner of k decides
+        if (warp == 0) {
+            for (int ks = 0; ks < spc; ++ks) {
+                const int k = k0 + ks;
+                uint32_t A = 0u;
+                if (((k ^ (int)t) & 1) == 0 && k + 1 < M) {
+                    const int kr = (ks + 1 < spc) ? rank : rank + 1;
+                    const int ksr = (ks + 1 < spc) ? ks + 1 : 0;
+                    int32_t *Er = cluster.map_shared_rank(Es, kr);
+                    const int e0 = Es[ks * 32 + lane], e1 = Er[ksr * 32 + lane];
+                    bool ok;
+                    if (e1 >= e0) {
+                        ok = true;
+                    } else {
+                        const int d = (e0 - e1) / 4;
+                        const uint32_t th = (d <= a.dmax) ? a.thr_pair[(size_t)k * (a.dmax + 1) + d] : 0u;
+                        const uint4 w = philox4x32_10(make_uint4((uint32_t)k, tt, group_rid0 + lane, 1u), a.key);
+                        ok = (th == kAlways) || (w.x < th);
+                    }
+                    A = __ballot_sync(kFull, ok) & valid;
+                    if (lane == 0 && A) atomicAdd(&a.swaps[k], (unsigned long long)__popc(A));
+                }
+                if (lane == 0) Amask[ks] = A;
+            }
+        }
+        __syncthreads();
+        for (int ks = 0; ks < spc; ++ks) {
+            const uint32_t A = Amask[ks];
+            if (!A) continue;  // uniform across the CTA
+            const int kr = (ks + 1 < spc) ? rank : rank + 1;
+            const int ksr = (ks + 1 < spc) ? ks + 1 : 0;
+            uint32_t *Sr = cluster.map_shared_rank(S, kr) + ksr * V;
+            uint32_t *Sl = S + ks * V;
+            for (int i = tid; i < V; i += blockDim.x) {
+                const uint32_t d = (Sl[i] ^ Sr[i]) & A;
+                Sl[i] ^= d;
+                Sr[i] ^= d;
+            }
+            if (tid < 32 && ((A >> tid) & 1u)) {
+                int32_t *Er = cluster.map_shared_rank(Es, kr);
+                int32_t *Lr = cluster.map_shared_rank(Ls, kr);
+                const int32_t te = Es[ks * 32 + tid];
+                Es[ks * 32 + tid] = Er[ksr * 32 + tid];
+                Er[ksr * 32 + tid] = te;
+                const int32_t tl = Ls[ks * 32 + tid];
+                Ls[ks * 32 + tid] = Lr[ksr * 32 + tid];
+                Lr[ksr * 32 + tid] = tl;
+            }
+        }
+        cluster.sync();  // exchanges complete everywhere
+        // ---- round trips / lowest energy per replica (by label)
+        for (int q = tid; q < spc * 32; q += blockDim.x) {
+            const int ks = q >> 5, b = q & 31;
+            if (!((valid >> b) & 1u)) continue;
+            const int lbl = Ls[q], E = Es[q];
+            PtRt &r = a.rt[((size_t)g * M + lbl) * 32 + b];
+            if (E < r.e_min) r.e_min = E;
+            if (a.count_rt) {
+                const int eg = a.bounds[((size_t)g * 32 + b) * 2 + 0];
+                const int ehot = a.bounds[((size_t)g * 32 + b) * 2 + 1];
+                if (r.phase == 0) {
+                    if (E >= ehot) { r.t_first = (int64_t)t; r.phase = 1; }
+                } else if (r.phase == 1) {
+                    if (E <= eg) r.phase = 2;
+                } else {
+                    if (E >= ehot) { r.n_rt += 1; r.t_last = (int64_t)t; r.phase = 1; }
+                }
+            }
+            (void)ks;
+        }
+        __syncthreads();
+    }
+    // ---- write back
+    for (int k = tid; k < spc * V; k += blockDim.x) a.spins[((size_t)g * M + k0) * V + k] = S[k];
+    for (int k = tid; k < spc * 32; k += blockDim.x) {
+        a.E[((size_t)g * M + k0) * 32 + k] = Es[k];
+        a.label[((size_t)g * M + k0) * 32 + k] = Ls[k];
+    }
+    cluster.sync();
+}
+
+// initial state: couplings and per-slot random spins from the seed (or the caller), energies
+// by full recomputation, labels = slot.  One warp per (group, slot).
+template <int DIM, int L>
+__global__ void pt_init_kernel(uint32_t *spins, uint32_t *bonds, int32_t *E, int32_t *label,
+                               const int8_t *Jin, int M, int n_real, uint32_t rid0, PhiloxKey key) {
+    using G = PtGeo<DIM, L>;
+    constexpr int V = G::V, NB = G::NB;
+    const int g = blockIdx.x / M, k = blockIdx.x % M, lane = threadIdx.x;
+    const uint32_t rid = rid0 + 32u * g + lane;
+    const bool act = (int)(32 * g + lane) < n_real;
+    uint32_t *sp = spins + ((size_t)g * M + k) * V;
+    uint32_t *bd = bonds + (size_t)g * NB;
+    if (k == 0) {
+        for (int j0 = 0; j0 < NB; j0 += 4) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), 0u, rid, 3u), key);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = j0 + jj;
+                if (j < NB) {
+                    const bool neg = act && (Jin ? (Jin[(size_t)(32 * g + lane) * NB + j] < 0)
+                                                 : ((uint4_get(w, jj) >> 31) != 0));
+                    const uint32_t m = __ballot_sync(kFull, neg);
+                    if (lane == 0) bd[j] = m;
+                }
+            }
+        }
+    }
+    for (int i0 = 0; i0 < V; i0 += 4) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), 0u, rid, 2u | ((uint32_t)k << 8)), key);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int i = i0 + jj;
+            if (i < V) {
+                const bool neg = act && ((uint4_get(w, jj) >> 31) != 0);
+                const uint32_t m = __ballot_sync(kFull, neg);
+                if (lane == 0) sp[i] = m;
+            }
+        }
+    }
+    label[((size_t)g * M + k) * 32 + lane] = k;
+}
+
+// energies of every (group, slot) from scratch; one warp per (group, slot)
+template <int DIM, int L>
+__global__ void pt_energy_kernel(const uint32_t *spins, const uint32_t *bonds, int32_t *E, int M) {
+    using G = PtGeo<DIM, L>;
+    constexpr int V = G::V, NB = G::NB;
+    const int g = blockIdx.x / M, k = blockIdx.x % M, lane = threadIdx.x;
+    const uint32_t *sp = spins + ((size_t)g * M + k) * V;
+    const uint32_t *bd = bonds + (size_t)g * NB;
+    int u = 0;
+    for (int i = 0; i < V; ++i)
+        for (int d = 0; d < DIM; ++d) {
+            const uint32_t w = sp[i] ^ sp[pt_nbr<DIM, L>(i, d, +1)] ^ bd[i * DIM + d];
+            u += (w >> lane) & 1u;
+        }
+    E[((size_t)g * M + k) * 32 + lane] = 2 * u - NB;
+}
+
+template <int DIM, int L>
+cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, uint64_t n_sweeps,
+                          int count_rt) {
+    using G = PtGeo<DIM, L>;
+    if (what == 0) {
+        pt_init_kernel<DIM, L><<<p->n_groups * p->M, 32, 0, ctx->stream>>>(
+            p->d_spins, p->d_bonds, p->d_E, p->d_label, dJ, p->M, p->n_real, p->rid0, ctx->key);
+        pt_energy_kernel<DIM, L><<<p->n_groups * p->M, 32, 0, ctx->stream>>>(p->d_spins, p->d_bonds, p->d_E, p->M);
+        return cudaGetLastError();
+    }
+    PtArgs a;
+    a.spins = p->d_spins;
+    a.bonds = p->d_bonds;
+    a.E = p->d_E;
+    a.label = p->d_label;
+    a.rt = p->d_rt;
+    a.bounds = p->d_bounds;
+    a.thr_k = p->d_thr_k;
+    a.thr_pair = p->d_thr_pair;
+    a.swaps = p->d_swaps;
+    a.M = p->M;
+    a.spc = p->M / p->cs;
+    a.dmax = p->dmax;
+    a.n_real = p->n_real;
+    a.rid0 = p->rid0;
+    a.t0 = p->t;
+    a.n_sweeps = n_sweeps;
+    a.count_rt = count_rt;
+    a.key = ctx->key;
+    const size_t smem = (size_t)(a.spc * G::V + G::NB + a.spc * 32 * 2 + a.spc * 8 + a.spc) * 4;
+    cudaError_t e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(p->n_groups * p->cs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p->cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pt_kernel<DIM, L>, a);
+}
+
+cudaError_t pt_dispatch(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, uint64_t n_sweeps, int count_rt) {
+#define PT_CASE(D, LL) \
+    if (p->dim == D && p->L == LL) return pt_launch_all<D, LL>(p, dJ, ctx, what, n_sweeps, count_rt);
+    PT_CASE(3, 4) PT_CASE(3, 6) PT_CASE(3, 8) PT_CASE(3, 10) PT_CASE(3, 12)
+    PT_CASE(2, 4) PT_CASE(2, 6) PT_CASE(2, 8) PT_CASE(2, 10) PT_CASE(2, 12)
+#undef PT_CASE
+    return cudaErrorInvalidValue;
+}
+
+__global__ void pt_tables_kernel(const double *beta, int M, int dim, int dmax, uint32_t *thr_k, uint32_t *thr_pair) {
+    const int z = 2 * dim;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    auto quant = [](double p) -> uint32_t {
+        if (p >= 1.0) return kAlways;
+        const double q = floor(p * 4294967296.0);
+        return (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
+    };
+    if (idx < M * 8) {
+        const int k = idx / 8, n = idx % 8;
+        uint32_t v = 0u;
+        if (n <= z) {
+            const int dE = 2 * z - 4 * n;
+            v = (dE <= 0) ? kAlways : quant(exp(-beta[k] * (double)dE));
+        }
+        thr_k[idx] = v;
+    }
+    const int np = (M - 1) * (dmax + 1);
+    if (idx < np) {
+        const int k = idx / (dmax + 1), d = idx % (dmax + 1);
+        thr_pair[idx] = (d == 0) ? kAlways : quant(exp(-(beta[k + 1] - beta[k]) * 4.0 * (double)d));
+    }
+}
+
+}  // namespace
 
 void pt_release(ea_ctx *ctx) {
     if (!ctx || !ctx->pt) return;
-    delete ctx->pt;
+    PtState *p = ctx->pt;
+    void *ptrs[] = {p->d_spins, p->d_bonds, p->d_E, p->d_label, p->d_rt, p->d_bounds,
+                    p->d_thr_k, p->d_thr_pair, p->d_swaps, p->d_err};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
     ctx->pt = nullptr;
+}
+
+#define PT_CUDA(call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, int M, const double *betas,
+                       const int8_t *couplings_or_null) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (dim != 2 && dim != 3) return fail(EA_EINVAL, "dim must be 2 or 3");
+    if (L < 4 || L > 12 || (L & 1)) return fail(EA_EINVAL, "PT needs an even L in [4, 12] (checkerboard)");
+    if (n_real <= 0) return fail(EA_EINVAL, "n_real must be positive");
+    if (rid0 % 32) return fail(EA_EINVAL, "rid0 must be a multiple of 32 (realizations are packed 32 per word)");
+    if (M < 2 || M > 64) return fail(EA_EINVAL, "M must be in [2, 64]");
+    if (!betas) return fail(EA_EINVAL, "null betas");
+    for (int k = 0; k + 1 < M; ++k)
+        if (!(betas[k + 1] > betas[k])) return fail(EA_EINVAL, "betas must increase with the slot index");
+    PT_CUDA(cudaSetDevice(ctx->device));
+    pt_release(ctx);
+    PtState *p = new PtState();
+    ctx->pt = p;
+    p->dim = dim;
+    p->L = L;
+    p->V = volume_of(dim, L);
+    p->nb = dim * p->V;
+    p->M = M;
+    p->n_real = n_real;
+    p->n_groups = (n_real + 31) / 32;
+    p->rid0 = rid0;
+    p->dmax = p->nb / 2;
+    p->betas.assign(betas, betas + M);
+    p->cs = 1;
+    for (int c : {8, 4, 2})
+        if (M % c == 0) { p->cs = c; break; }
+    const size_t G = p->n_groups;
+    auto alloc = [&](void **ptr, size_t bytes) -> int {
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) return fail(EA_ENOMEM, "PT allocation of %zu bytes failed", bytes);
+        cudaMemsetAsync(*ptr, 0, bytes, ctx->stream);
+        return EA_OK;
+    };
+    int rc;
+    if ((rc = alloc((void **)&p->d_spins, G * M * p->V * 4)) || (rc = alloc((void **)&p->d_bonds, G * p->nb * 4)) ||
+        (rc = alloc((void **)&p->d_E, G * M * 32 * 4)) || (rc = alloc((void **)&p->d_label, G * M * 32 * 4)) ||
+        (rc = alloc((void **)&p->d_rt, G * M * 32 * sizeof(PtRt))) ||
+        (rc = alloc((void **)&p->d_bounds, G * 32 * 2 * 4)) || (rc = alloc((void **)&p->d_thr_k, M * 8 * 4)) ||
+        (rc = alloc((void **)&p->d_thr_pair, (size_t)(M - 1) * (p->dmax + 1) * 4)) ||
+        (rc = alloc((void **)&p->d_swaps, (M - 1) * 8)) || (rc = alloc((void **)&p->d_err, 4))) {
+        pt_release(ctx);
+        return rc;
+    }
+    // tables (FP64 exp -> u32), bounds default: never reached
+    void *scr;
+    if ((rc = ctx_scratch(ctx, (size_t)M * 8 + (size_t)n_real * p->nb + 256, &scr))) return rc;
+    double *d_beta = (double *)scr;
+    PT_CUDA(cudaMemcpyAsync(d_beta, betas, M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    const int ntab = std::max(M * 8, (M - 1) * (p->dmax + 1));
+    pt_tables_kernel<<<(ntab + 255) / 256, 256, 0, ctx->stream>>>(d_beta, M, dim, p->dmax, p->d_thr_k, p->d_thr_pair);
+    PT_CUDA(cudaGetLastError());
+    const int8_t *dJ = nullptr;
+    if (couplings_or_null) {
+        dJ = (const int8_t *)((char *)scr + (((size_t)M * 8 + 127) & ~(size_t)127));
+        PT_CUDA(cudaMemcpyAsync((void *)dJ, couplings_or_null, (size_t)n_real * p->nb, cudaMemcpyHostToDevice,
+                                ctx->stream));
+    }
+    std::vector<int32_t> hb(G * 32 * 2);
+    for (size_t q = 0; q < G * 32; ++q) {
+        hb[2 * q] = -(1 << 30);   // e_g: never reached
+        hb[2 * q + 1] = 1 << 30;  // e_hot: never reached
+    }
+    PT_CUDA(cudaMemcpyAsync(p->d_bounds, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    PT_CUDA(pt_dispatch(p, dJ, ctx, 0, 0, 0));
+    // round-trip records start at phase 0 with e_min = the initial energy
+    std::vector<int32_t> hE(G * M * 32);
+    PT_CUDA(cudaMemcpyAsync(hE.data(), p->d_E, hE.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<PtRt> hr(G * M * 32);
+    for (size_t gg = 0; gg < G; ++gg)
+        for (int k = 0; k < M; ++k)
+            for (int b = 0; b < 32; ++b) {
+                PtRt &r = hr[(gg * M + k) * 32 + b];  // label k starts at slot k
+                r.phase = 0;
+                r.n_rt = 0;
+                r.t_first = -1;
+                r.t_last = -1;
+                r.e_min = hE[(gg * M + k) * 32 + b];
+                r.pad = 0;
+            }
+    PT_CUDA(cudaMemcpyAsync(p->d_rt, hr.data(), hr.size() * sizeof(PtRt), cudaMemcpyHostToDevice, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    p->t = 0;
+    return EA_OK;
+}
+
+extern "C" int pt_set_rt_bounds(ea_ctx *ctx, const int32_t *e_g, const int32_t *e_hot) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    if (!e_g || !e_hot) return fail(EA_EINVAL, "null bounds");
+    PtState *p = ctx->pt;
+    std::vector<int32_t> hb((size_t)p->n_groups * 64, 0);
+    for (size_t q = 0; q < (size_t)p->n_groups * 32; ++q) {
+        const bool in = q < (size_t)p->n_real;
+        hb[2 * q] = in ? e_g[q] : -(1 << 30);
+        hb[2 * q + 1] = in ? e_hot[q] : (1 << 30);
+    }
+    PT_CUDA(cudaMemcpyAsync(p->d_bounds, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int pt_run(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    PtState *p = ctx->pt;
+    if (p->t + n_sweeps > (1ull << 32)) return fail(EA_EINVAL, "sweep counter would exceed 2^32");
+    if (n_sweeps == 0) return EA_OK;
+    PT_CUDA(pt_dispatch(p, nullptr, ctx, 1, n_sweeps, count_roundtrips));
+    p->t += n_sweeps;
+    return EA_OK;
+}
+
+extern "C" int pt_get_state(ea_ctx *ctx, int8_t *spins, int32_t *E, int32_t *labels, uint64_t *t) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    PtState *p = ctx->pt;
+    const size_t G = p->n_groups, M = p->M, V = p->V;
+    std::vector<uint32_t> hs;
+    std::vector<int32_t> hE(G * M * 32), hL(G * M * 32);
+    if (spins) {
+        hs.resize(G * M * V);
+        PT_CUDA(cudaMemcpyAsync(hs.data(), p->d_spins, hs.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    PT_CUDA(cudaMemcpyAsync(hE.data(), p->d_E, hE.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(cudaMemcpyAsync(hL.data(), p->d_label, hL.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < p->n_real; ++r) {
+        const size_t g = r / 32, b = r % 32;
+        for (size_t k = 0; k < M; ++k) {
+            if (E) E[r * M + k] = hE[(g * M + k) * 32 + b];
+            if (labels) labels[r * M + k] = hL[(g * M + k) * 32 + b];
+            if (spins)
+                for (size_t i = 0; i < V; ++i)
+                    spins[(r * M + k) * V + i] = ((hs[(g * M + k) * V + i] >> b) & 1u) ? -1 : 1;
+        }
+    }
+    if (t) *t = p->t;
+    return EA_OK;
+}
+
+extern "C" int pt_get_roundtrips(ea_ctx *ctx, ea_pt_stats *out, int reset) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    if (!out) return fail(EA_EINVAL, "null output");
+    PtState *p = ctx->pt;
+    const size_t G = p->n_groups, M = p->M;
+    std::vector<PtRt> hr(G * M * 32);
+    PT_CUDA(cudaMemcpyAsync(hr.data(), p->d_rt, hr.size() * sizeof(PtRt), cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < p->n_real; ++r) {
+        const size_t g = r / 32, b = r % 32;
+        for (size_t l = 0; l < M; ++l) {
+            const PtRt &s = hr[(g * M + l) * 32 + b];
+            ea_pt_stats &o = out[r * M + l];
+            o.n_rt = s.n_rt;
+            o.phase = s.phase;
+            o.t_first = s.t_first;
+            o.t_last = s.t_last;
+            o.e_min = s.e_min;
+            o.pad = 0;
+        }
+    }
+    if (reset) {
+        std::vector<int32_t> hE(G * M * 32), hL(G * M * 32);
+        PT_CUDA(cudaMemcpyAsync(hE.data(), p->d_E, hE.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        PT_CUDA(cudaMemcpyAsync(hL.data(), p->d_label, hL.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        PT_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (size_t g = 0; g < G; ++g)
+            for (size_t k = 0; k < M; ++k)
+                for (int b = 0; b < 32; ++b) {
+                    const int lbl = hL[(g * M + k) * 32 + b];
+                    PtRt &s = hr[(g * M + lbl) * 32 + b];
+                    s.phase = 0;
+                    s.n_rt = 0;
+                    s.t_first = -1;
+                    s.t_last = -1;
+                    s.e_min = hE[(g * M + k) * 32 + b];
+                }
+        PT_CUDA(cudaMemcpyAsync(p->d_rt, hr.data(), hr.size() * sizeof(PtRt), cudaMemcpyHostToDevice, ctx->stream));
+        PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return EA_OK;
+}
+
+extern "C" int pt_get_swap_counts(ea_ctx *ctx, uint64_t *out) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    if (!out) return fail(EA_EINVAL, "null output");
+    PtState *p = ctx->pt;
+    PT_CUDA(cudaMemcpyAsync(out, p->d_swaps, (p->M - 1) * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
 }

@@ -69,6 +69,12 @@ SIGNATURES = {
     "get_roundtrips": (_i, [P, _i, _i, P, _i]),
     "get_state": (_i, [P, _i, _i, P, _i, P, P]),
     "ea_synchronize": (_i, [P]),
+    "pt_init": (_i, [P, _i, _i, _i, _u32, _i, P, P]),
+    "pt_set_rt_bounds": (_i, [P, P, P]),
+    "pt_run": (_i, [P, _u64, _i]),
+    "pt_get_state": (_i, [P, P, P, P, P]),
+    "pt_get_roundtrips": (_i, [P, P, _i]),
+    "pt_get_swap_counts": (_i, [P, P]),
 }
 
 _lib = None
@@ -221,3 +227,42 @@ class Context:
 
     def synchronize(self):
         check(lib().ea_synchronize(self._h))
+
+    # a6 + a7: parallel tempering
+    def pt_init(self, dim: int, L: int, n_real: int, betas, rid0: int = 0,
+                couplings: np.ndarray | None = None):
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        J = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
+        check(lib().pt_init(self._h, dim, L, n_real, rid0, b.shape[0], _p(b), _p(J)))
+        self._pt = (dim, L, n_real, b.shape[0])
+
+    def pt_set_rt_bounds(self, e_g, e_hot):
+        eg = np.ascontiguousarray(e_g, dtype=np.int32)
+        eh = np.ascontiguousarray(e_hot, dtype=np.int32)
+        check(lib().pt_set_rt_bounds(self._h, _p(eg), _p(eh)))
+
+    def pt_run(self, n_sweeps: int, count_roundtrips: bool = False):
+        check(lib().pt_run(self._h, n_sweeps, int(count_roundtrips)))
+
+    def pt_state(self, spins: bool = True):
+        dim, L, n, M = self._pt
+        V = L ** dim
+        S = np.zeros((n, M, V), dtype=np.int8) if spins else None
+        E = np.zeros((n, M), dtype=np.int32)
+        lab = np.zeros((n, M), dtype=np.int32)
+        t = ctypes.c_uint64(0)
+        check(lib().pt_get_state(self._h, _p(S), _p(E), _p(lab), ctypes.byref(t)))
+        return S, E, lab, t.value
+
+    def pt_roundtrips(self, reset: bool = False):
+        dim, L, n, M = self._pt
+        out = (ea_pt_stats * (n * M))()
+        check(lib().pt_get_roundtrips(self._h, out, int(reset)))
+        return [[{f: getattr(out[r * M + l], f) for f, _ in ea_pt_stats._fields_ if f != "pad"}
+                 for l in range(M)] for r in range(n)]
+
+    def pt_swap_counts(self):
+        M = self._pt[3]
+        out = np.zeros(M - 1, dtype=np.uint64)
+        check(lib().pt_get_swap_counts(self._h, _p(out)))
+        return out

@@ -20,7 +20,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ("ea_init_disorder", "muca_run_sweeps", "muca_update_weights", "get_histograms",
-                     "get_roundtrips"):
+                     "get_roundtrips", "pt_run"):
         assert required in names, required
 
 
