@@ -133,6 +133,22 @@ int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g);
  * t + n_sweeps <= 2^32 for every chain.  Asynchronous on the context stream. */
 int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
 
+/* a8 -- launch configuration of muca_run_sweeps.  persistent = 0: one thread block (two
+ * warps) per tile of 32 chains; persistent = 1: a grid sized to the device's resident
+ * capacity whose blocks pull tiles from a work queue, longest lattices first (for batches
+ * of uneven L).  sweeps_per_launch > 0 splits a run into launches of at most that many
+ * sweeps (0 = one launch).  Results do not depend on either setting. */
+int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch);
+
+/* a8 -- captures n_iter iterations of [muca_run_sweeps(sweeps_per_iter, count_roundtrips),
+ * then muca_update_weights if update_weights] into a CUDA graph on the context stream (which
+ * must not be the legacy default stream).  ea_graph_launch replays it; ea_graph_release
+ * frees it.  Replays see the launch configuration at capture time. */
+int ea_graph_capture(ea_ctx *ctx, int n_iter, uint64_t sweeps_per_iter, int count_roundtrips,
+                     int update_weights);
+int ea_graph_launch(ea_ctx *ctx, int replays);
+int ea_graph_release(ea_ctx *ctx);
+
 /* a4 -- one step of the weight iteration (Sec. II, iterative procedure after Janke 2003,
  * with shaped histograms): ln W <- ln W + ln P_SH(E) - ln max(H(E), 1), shifted to 0 at
  * b_top, with P_SH from the chain's kind (flat: 1, power law: Eq. "power_law" with E_g =

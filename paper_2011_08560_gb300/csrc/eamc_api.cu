@@ -123,8 +123,10 @@ __global__ void unpack_spins(const TileDesc *__restrict__ tiles, const int32_t *
     const int slot = slot_of[c];
     const TileDesc td = tiles[slot / kTile];
     const int lane = slot % kTile;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < td.V; i += gridDim.x * blockDim.x)
-        out[(size_t)c * stride + i] = ((spins[td.spin_off + i] >> lane) & 1u) ? int8_t(-1) : int8_t(1);
+    // the whole row is written: sites beyond this chain's V read as 0
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < stride; i += gridDim.x * blockDim.x)
+        out[(size_t)c * stride + i] =
+            (i >= td.V) ? int8_t(0) : (((spins[td.spin_off + i] >> lane) & 1u) ? int8_t(-1) : int8_t(1));
 }
 
 __global__ void set_eg_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
@@ -267,6 +269,28 @@ int eamc::ctx_refresh_chains(ea_ctx *ctx) {
     return EA_OK;
 }
 
+// tile ids ordered by decreasing lattice volume (longest tiles first, for the work queue)
+int eamc::ctx_rebuild_order(ea_ctx *ctx) {
+    const size_t n = ctx->tiles.size();
+    std::vector<int32_t> order(n);
+    for (size_t t = 0; t < n; ++t) order[t] = (int32_t)t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return ctx->tiles[a].V > ctx->tiles[b].V; });
+    if (n > ctx->order_cap) {
+        if (ctx->d_order) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->d_order);
+        }
+        ctx->d_order = nullptr;
+        if (cudaMalloc(&ctx->d_order, n * sizeof(int32_t)) != cudaSuccess)
+            return fail(EA_ENOMEM, "tile order allocation failed");
+        ctx->order_cap = n;
+    }
+    EA_CUDA(cudaMemcpyAsync(ctx->d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
 extern "C" int ea_create(ea_ctx **out, int device, void *cuda_stream, uint64_t seed) {
     if (!out) return fail(EA_EINVAL, "null output pointer");
     int ndev = 0;
@@ -281,6 +305,12 @@ extern "C" int ea_create(ea_ctx **out, int device, void *cuda_stream, uint64_t s
     cudaError_t e = cudaMalloc(&ctx->d_err, sizeof(int));
     if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaMalloc"); }
     cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_queue, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->d_err);
+        delete ctx;
+        return fail(EA_ENOMEM, "queue allocation failed");
+    }
     *out = ctx;
     return EA_OK;
 }
@@ -290,6 +320,10 @@ extern "C" void ea_destroy(ea_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     pt_release(ctx);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->d_order) cudaFree(ctx->d_order);
+    if (ctx->d_queue) cudaFree(ctx->d_queue);
     void *ptrs[] = {ctx->d_tiles, ctx->d_slots, ctx->d_spins,   ctx->d_bonds, ctx->d_lnW,
                     ctx->d_hist,  ctx->d_thr ? ctx->d_thr - kThrPad : nullptr,
                     ctx->d_scratch, ctx->d_err, ctx->d_Jin};
@@ -400,6 +434,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
         ctx->chain_btop.push_back(0);
     }
     if ((rc = ctx_refresh_chains(ctx))) return rc;
+    if ((rc = ctx_rebuild_order(ctx))) return rc;
     // flat weights (ln W = 0 already) -> thresholds
     EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW,
                             ctx->d_thr, ctx->stream));
@@ -544,15 +579,94 @@ extern "C" int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g) {
     return EA_OK;
 }
 
+static int enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
+    const int nt = (int)ctx->tiles.size();
+    const uint64_t chunk = ctx->sweeps_per_launch ? ctx->sweeps_per_launch : n_sweeps;
+    for (uint64_t done = 0; done < n_sweeps; done += chunk) {
+        const uint64_t now = std::min(chunk, n_sweeps - done);
+        if (ctx->persistent) {
+            const int per_sm = sweep_blocks_per_sm(ctx->dim, ctx->sweep_smem);
+            const int grid = std::min(nt, per_sm * std::max(ctx->n_sm, 1));
+            EA_CUDA(launch_sweeps(ctx->d_tiles, ctx->d_order, grid, nt, ctx->d_queue, ctx->dim, ctx->sweep_smem,
+                                  ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key,
+                                  count_roundtrips, ctx->stream));
+        } else {
+            EA_CUDA(launch_sweeps(ctx->d_tiles, nullptr, nt, nt, nullptr, ctx->dim, ctx->sweep_smem, ctx->d_slots,
+                                  ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key,
+                                  count_roundtrips, ctx->stream));
+        }
+    }
+    return EA_OK;
+}
+
 extern "C" int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
     if (!ctx) return fail(EA_EINVAL, "null context");
     if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains: call ea_init_disorder first");
     if (n_sweeps > (1ull << 32) || ctx->max_t_host + n_sweeps > (1ull << 32))
         return fail(EA_EINVAL, "sweep counter would exceed 2^32");
-    EA_CUDA(launch_sweeps(ctx->d_tiles, nullptr, (int)ctx->tiles.size(), ctx->dim, ctx->sweep_smem,
-                          ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, n_sweeps,
-                          ctx->key, count_roundtrips, ctx->stream));
+    int rc = enqueue_sweeps(ctx, n_sweeps, count_roundtrips);
+    if (rc) return rc;
     ctx->max_t_host += n_sweeps;
+    return EA_OK;
+}
+
+extern "C" int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    ctx->persistent = persistent ? 1 : 0;
+    ctx->sweeps_per_launch = sweeps_per_launch;
+    return EA_OK;
+}
+
+extern "C" int ea_graph_capture(ea_ctx *ctx, int n_iter, uint64_t sweeps_per_iter, int count_roundtrips,
+                                int update_weights) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains: call ea_init_disorder first");
+    if (!ctx->stream) return fail(EA_EINVAL, "graph capture needs a non-default stream");
+    if (n_iter <= 0 || sweeps_per_iter == 0) return fail(EA_EINVAL, "empty iteration graph");
+    if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    // attributes are set outside the capture (they are not stream work)
+    EA_CUDA(prepare_sweeps(ctx->dim, ctx->sweep_smem));
+    EA_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = EA_OK;
+    const int nt = (int)ctx->tiles.size();
+    for (int it = 0; it < n_iter && rc == EA_OK; ++it) {
+        rc = enqueue_sweeps(ctx, sweeps_per_iter, count_roundtrips);
+        if (rc == EA_OK && update_weights) {
+            cudaError_t e = launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->stream);
+            if (e == cudaSuccess) e = launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "update in capture");
+        }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphInstantiate"); }
+    ctx->graph = g;
+    ctx->graph_sweeps = (uint64_t)n_iter * sweeps_per_iter;
+    return EA_OK;
+}
+
+extern "C" int ea_graph_launch(ea_ctx *ctx, int replays) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (!ctx->graph_exec) return fail(EA_ESTATE, "no captured graph: call ea_graph_capture first");
+    if (replays < 0) return fail(EA_EINVAL, "negative replay count");
+    if (ctx->max_t_host + (uint64_t)replays * ctx->graph_sweeps > (1ull << 32))
+        return fail(EA_EINVAL, "sweep counter would exceed 2^32");
+    for (int r = 0; r < replays; ++r) EA_CUDA(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->max_t_host += (uint64_t)replays * ctx->graph_sweeps;
+    return EA_OK;
+}
+
+extern "C" int ea_graph_release(ea_ctx *ctx) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    ctx->graph_sweeps = 0;
     return EA_OK;
 }
 
@@ -638,7 +752,7 @@ extern "C" int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stri
     int8_t *d_sp = (int8_t *)scr;
     ea_chain_desc *d_desc = (ea_chain_desc *)((char *)scr + ((sbytes + 255) & ~(size_t)255));
     if (spins) {
-        dim3 grid((maxV + 255) / 256, n);
+        dim3 grid((stride + 255) / 256, n);
         unpack_spins<<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, d_slot, n, stride, ctx->d_spins, d_sp);
         EA_CUDA(cudaGetLastError());
         EA_CUDA(cudaMemcpyAsync(spins, d_sp, sbytes, cudaMemcpyDeviceToHost, ctx->stream));

@@ -40,6 +40,17 @@ struct ea_ctx {
     int *d_err = nullptr;
     int8_t *d_Jin = nullptr;
 
+    // a8: launch configuration of the sweep kernel and the captured iteration graph
+    int persistent = 0;               // 1: resident grid pulling tiles from a queue
+    uint64_t sweeps_per_launch = 0;   // 0: all requested sweeps in one launch
+    int n_sm = 0;
+    int32_t *d_order = nullptr;       // tile ids, longest tiles first
+    size_t order_cap = 0;
+    int *d_queue = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_sweeps = 0;        // sweeps one replay adds to every chain
+
     PtState *pt = nullptr;
 };
 
@@ -51,6 +62,7 @@ int ctx_check_range(ea_ctx *ctx, int chain0, int n);
 int ctx_range_meta(ea_ctx *ctx, int chain0, int n, size_t extra, void **scratch, int32_t **d_slot,
                    uint64_t **d_off, int32_t **d_len);
 int ctx_refresh_chains(ea_ctx *ctx);
+int ctx_rebuild_order(ea_ctx *ctx);
 }  // namespace eamc
 
 void pt_release(ea_ctx *ctx);

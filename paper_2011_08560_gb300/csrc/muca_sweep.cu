@@ -344,14 +344,14 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
 }
 
 // Two warps (consumer + producer) per tile of 32 chains; the tile's L selects the body.
+// Direct mode (queue == nullptr): block b sweeps tile tile_list[b] (or b).  Persistent mode:
+// a grid sized to the resident capacity pulls positions of tile_list (longest tiles first)
+// from the counter *queue until n_work positions are taken.
 template <int DIM>
-__global__ void __launch_bounds__(64, 1)
-muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ tile_list,
-                  SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
-                  const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
-                  uint32_t *__restrict__ hist, uint64_t n_sweeps, PhiloxKey key, int count_rt) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tile = tile_list ? tile_list[blockIdx.x] : (int)blockIdx.x;
+__device__ __forceinline__ void sweep_one(const TileDesc *__restrict__ tiles, int tile, SlotState *slots,
+                                          uint32_t *spins, const uint32_t *bonds, const uint32_t *thr,
+                                          uint32_t *hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
+                                          unsigned char *smem_raw) {
     const TileDesc td = tiles[tile];
 #define EAMC_CASE(LL)                                                                      \
     case LL:                                                                               \
@@ -364,6 +364,31 @@ muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict_
         default: break;
     }
 #undef EAMC_CASE
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(64, 1)
+muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ tile_list, int n_work,
+                  int *__restrict__ queue, SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
+                  const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
+                  uint32_t *__restrict__ hist, uint64_t n_sweeps, PhiloxKey key, int count_rt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (!queue) {
+        const int tile = tile_list ? tile_list[blockIdx.x] : (int)blockIdx.x;
+        sweep_one<DIM>(tiles, tile, slots, spins, bonds, thr, hist, n_sweeps, key, count_rt, smem_raw);
+        return;
+    }
+    __shared__ int s_pos;
+    for (;;) {
+        if (threadIdx.x == 0) s_pos = atomicAdd(queue, 1);
+        __syncthreads();
+        const int pos = s_pos;
+        __syncthreads();  // every thread has read s_pos before it is overwritten
+        if (pos >= n_work) break;
+        sweep_one<DIM>(tiles, tile_list[pos], slots, spins, bonds, thr, hist, n_sweeps, key, count_rt,
+                       smem_raw);
+        __syncthreads();  // both warps are done with this tile's shared memory
+    }
 }
 
 template <int DIM>
@@ -387,24 +412,46 @@ size_t smem_for(int L) {
 
 size_t sweep_smem_bytes(int dim, int L) { return dim == 3 ? smem_for<3>(L) : smem_for<2>(L); }
 
-cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, int n_blocks, int dim,
-                          size_t smem, SlotState *d_slots, uint32_t *d_spins, const uint32_t *d_bonds,
-                          const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key,
-                          int count_rt, cudaStream_t st) {
+// Raises the kernel's dynamic shared-memory limit when needed (a host call that is not stream
+// work, so it happens before any graph capture that launches the kernel).
+cudaError_t prepare_sweeps(int dim, size_t smem) {
+    static int set_limit[4] = {0, 0, 0, 0};
+    if ((int)smem <= set_limit[dim]) return cudaSuccess;
+    const cudaError_t e = dim == 3
+        ? cudaFuncSetAttribute(muca_sweep_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+        : cudaFuncSetAttribute(muca_sweep_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set_limit[dim] = (int)smem;
+    return e;
+}
+
+cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, int n_blocks, int n_work,
+                          int *d_queue, int dim, size_t smem, SlotState *d_slots, uint32_t *d_spins,
+                          const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
+                          PhiloxKey key, int count_rt, cudaStream_t st) {
     if (n_blocks <= 0 || n_sweeps == 0) return cudaSuccess;
     cudaError_t e;
+    if (d_queue) {
+        e = cudaMemsetAsync(d_queue, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = prepare_sweeps(dim, smem)) != cudaSuccess) return e;
     if (dim == 3) {
-        e = cudaFuncSetAttribute(muca_sweep_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        muca_sweep_kernel<3><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, d_slots, d_spins, d_bonds,
-                                                         d_thr, d_hist, n_sweeps, key, count_rt);
+        muca_sweep_kernel<3><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
+                                                         d_bonds, d_thr, d_hist, n_sweeps, key, count_rt);
     } else {
-        e = cudaFuncSetAttribute(muca_sweep_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        muca_sweep_kernel<2><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, d_slots, d_spins, d_bonds,
-                                                         d_thr, d_hist, n_sweeps, key, count_rt);
+        muca_sweep_kernel<2><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
+                                                         d_bonds, d_thr, d_hist, n_sweeps, key, count_rt);
     }
     return cudaGetLastError();
+}
+
+int sweep_blocks_per_sm(int dim, size_t smem) {
+    int nb = 0;
+    if (dim == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, muca_sweep_kernel<3>, 64, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, muca_sweep_kernel<2>, 64, smem);
+    return nb > 0 ? nb : 1;
 }
 
 }  // namespace eamc

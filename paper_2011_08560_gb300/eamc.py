@@ -69,6 +69,10 @@ SIGNATURES = {
     "get_roundtrips": (_i, [P, _i, _i, P, _i]),
     "get_state": (_i, [P, _i, _i, P, _i, P, P]),
     "ea_synchronize": (_i, [P]),
+    "muca_set_launch": (_i, [P, _i, _u64]),
+    "ea_graph_capture": (_i, [P, _i, _u64, _i, _i]),
+    "ea_graph_launch": (_i, [P, _i]),
+    "ea_graph_release": (_i, [P]),
     "pt_init": (_i, [P, _i, _i, _i, _u32, _i, P, P]),
     "pt_set_rt_bounds": (_i, [P, P, P]),
     "pt_run": (_i, [P, _u64, _i]),
@@ -227,6 +231,21 @@ class Context:
 
     def synchronize(self):
         check(lib().ea_synchronize(self._h))
+
+    # a8: launch configuration and the captured iteration graph
+    def set_launch(self, persistent: bool = False, sweeps_per_launch: int = 0):
+        check(lib().muca_set_launch(self._h, int(persistent), sweeps_per_launch))
+
+    def graph_capture(self, n_iter: int, sweeps_per_iter: int, count_roundtrips: bool = False,
+                      update_weights: bool = True):
+        check(lib().ea_graph_capture(self._h, n_iter, sweeps_per_iter, int(count_roundtrips),
+                                     int(update_weights)))
+
+    def graph_launch(self, replays: int = 1):
+        check(lib().ea_graph_launch(self._h, replays))
+
+    def graph_release(self):
+        check(lib().ea_graph_release(self._h))
 
     # a6 + a7: parallel tempering
     def pt_init(self, dim: int, L: int, n_real: int, betas, rid0: int = 0,
