@@ -134,11 +134,16 @@ int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g);
 int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
 
 /* a8 -- launch configuration of muca_run_sweeps.  persistent = 0: one thread block (two
- * warps) per tile of 32 chains; persistent = 1: a grid sized to the device's resident
- * capacity whose blocks pull tiles from a work queue, longest lattices first (for batches
+ * warps) per tile of 32 chains; persistent = 1: a grid of blocks_per_sm blocks per SM (0 = as
+ * many as fit) whose blocks pull tiles from a work queue, longest lattices first (for batches
  * of uneven L).  sweeps_per_launch > 0 splits a run into launches of at most that many
- * sweeps (0 = one launch).  Results do not depend on either setting. */
-int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch);
+ * sweeps (0 = one launch).  Results do not depend on any of these settings. */
+int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch, int blocks_per_sm);
+
+/* a8 / a9 -- every tile of linear size L runs multiplier x the requested sweeps in each
+ * muca_run_sweeps call (default 1), so a launch over tiles of uneven L can give small lattices
+ * proportionally more sweeps.  A chain's trajectory depends only on its own sweep count. */
+int muca_set_sweep_multiplier(ea_ctx *ctx, int L, int multiplier);
 
 /* a8 -- captures n_iter iterations of [muca_run_sweeps(sweeps_per_iter, count_roundtrips),
  * then muca_update_weights if update_weights] into a CUDA graph on the context stream (which
@@ -161,6 +166,17 @@ int muca_update_weights(ea_ctx *ctx);
  * EA_FLAT..EA_CANON, then re-quantises.  The new kind and parameters are recorded. */
 int muca_build_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
                         double pole_dE, double beta);
+
+/* a9 -- serving support.  Re-initialises the listed chains (host int32 chain indices)
+ * in place as new jobs: realization rids[k] with stream streams[k] (host uint32 arrays),
+ * couplings and spins drawn from the seed, deterministic descent to E <= E_top, flat weights,
+ * kind EA_FLAT, sweep counter 0, cleared histogram and round trips.  The chain keeps its L.
+ * Other chains of the context are untouched, so their trajectories do not change. */
+int ea_reset_chains(ea_ctx *ctx, const int32_t *chains, int n, const uint32_t *rids,
+                    const uint32_t *streams);
+
+/* a4 for the listed chains only (host int32 chain indices); see muca_update_weights. */
+int muca_update_weights_subset(ea_ctx *ctx, const int32_t *chains, int n);
 
 /* Histograms H[c*stride + b], b = 0..b_top(c); reset != 0 clears them afterwards. */
 int get_histograms(ea_ctx *ctx, int chain0, int n, uint32_t *out, int stride, int reset);

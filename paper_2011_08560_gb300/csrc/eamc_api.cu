@@ -363,7 +363,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
         td.V = V;
         td.B = B;
         td.n_active = std::min(kTile, n - t * kTile);
-        td.pad0 = 0;
+        td.sweep_mul = 1;
         td.w_base = w_used;
         td.spin_off = spin_used;
         td.bond_off = bond_used;
@@ -585,7 +585,8 @@ static int enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) 
     for (uint64_t done = 0; done < n_sweeps; done += chunk) {
         const uint64_t now = std::min(chunk, n_sweeps - done);
         if (ctx->persistent) {
-            const int per_sm = sweep_blocks_per_sm(ctx->dim, ctx->sweep_smem);
+            int per_sm = sweep_blocks_per_sm(ctx->dim, ctx->sweep_smem);
+            if (ctx->blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->blocks_per_sm);
             const int grid = std::min(nt, per_sm * std::max(ctx->n_sm, 1));
             EA_CUDA(launch_sweeps(ctx->d_tiles, ctx->d_order, grid, nt, ctx->d_queue, ctx->dim, ctx->sweep_smem,
                                   ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key,
@@ -602,18 +603,38 @@ static int enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) 
 extern "C" int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
     if (!ctx) return fail(EA_EINVAL, "null context");
     if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains: call ea_init_disorder first");
-    if (n_sweeps > (1ull << 32) || ctx->max_t_host + n_sweeps > (1ull << 32))
+    uint64_t mul = 1;
+    for (const TileDesc &td : ctx->tiles) mul = std::max<uint64_t>(mul, (uint64_t)td.sweep_mul);
+    if (n_sweeps > (1ull << 32) || ctx->max_t_host + n_sweeps * mul > (1ull << 32))
         return fail(EA_EINVAL, "sweep counter would exceed 2^32");
     int rc = enqueue_sweeps(ctx, n_sweeps, count_roundtrips);
     if (rc) return rc;
-    ctx->max_t_host += n_sweeps;
+    ctx->max_t_host += n_sweeps * mul;
     return EA_OK;
 }
 
-extern "C" int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch) {
+extern "C" int muca_set_sweep_multiplier(ea_ctx *ctx, int L, int multiplier) {
     if (!ctx) return fail(EA_EINVAL, "null context");
+    if (multiplier < 1 || multiplier > 4096) return fail(EA_EINVAL, "multiplier must be in [1, 4096]");
+    bool any = false;
+    for (size_t t = 0; t < ctx->tiles.size(); ++t)
+        if (ctx->tiles[t].L == L) {
+            ctx->tiles[t].sweep_mul = multiplier;
+            EA_CUDA(cudaMemcpyAsync(&ctx->d_tiles[t].sweep_mul, &ctx->tiles[t].sweep_mul, sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+            any = true;
+        }
+    if (!any) return fail(EA_EINVAL, "no tile of L=%d", L);
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch, int blocks_per_sm) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (blocks_per_sm < 0) return fail(EA_EINVAL, "blocks_per_sm must be >= 0");
     ctx->persistent = persistent ? 1 : 0;
     ctx->sweeps_per_launch = sweeps_per_launch;
+    ctx->blocks_per_sm = blocks_per_sm;
     return EA_OK;
 }
 
@@ -646,7 +667,9 @@ extern "C" int ea_graph_capture(ea_ctx *ctx, int n_iter, uint64_t sweeps_per_ite
     e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(e, "cudaGraphInstantiate"); }
     ctx->graph = g;
-    ctx->graph_sweeps = (uint64_t)n_iter * sweeps_per_iter;
+    uint64_t mul = 1;
+    for (const TileDesc &td : ctx->tiles) mul = std::max<uint64_t>(mul, (uint64_t)td.sweep_mul);
+    ctx->graph_sweeps = (uint64_t)n_iter * sweeps_per_iter * mul;
     return EA_OK;
 }
 
@@ -703,6 +726,65 @@ extern "C" int muca_build_ensemble(ea_ctx *ctx, int chain0, int n, int kind, dou
     EA_CUDA(launch_build_ensemble(ctx->d_tiles, nt, ctx->d_slots, d_sel, kind, alpha, pole_dE, beta,
                                   ctx->d_lnW, ctx->stream));
     EA_CUDA(launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+// chain list -> device slot list (after `extra` bytes of scratch)
+static int upload_slots(ea_ctx *ctx, const int32_t *chains, int n, size_t extra, void **scr, int32_t **d_slot) {
+    std::vector<int32_t> hs(n);
+    for (int k = 0; k < n; ++k) {
+        if (chains[k] < 0 || chains[k] >= (int)ctx->chain_slot.size())
+            return fail(EA_EINVAL, "chain %d outside [0, %zu)", chains[k], ctx->chain_slot.size());
+        hs[k] = ctx->chain_slot[chains[k]];
+    }
+    const size_t a = (extra + 255) & ~(size_t)255;
+    int rc = ctx_scratch(ctx, a + (size_t)n * sizeof(int32_t) + 256, scr);
+    if (rc) return rc;
+    *d_slot = (int32_t *)((char *)*scr + a);
+    EA_CUDA(cudaMemcpyAsync(*d_slot, hs.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int ea_reset_chains(ea_ctx *ctx, const int32_t *chains, int n, const uint32_t *rids,
+                               const uint32_t *streams) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (n < 0 || (n > 0 && (!chains || !rids || !streams))) return fail(EA_EINVAL, "bad chain list");
+    if (n == 0) return EA_OK;
+    for (int k = 0; k < n; ++k)
+        if (streams[k] >= (1u << 24)) return fail(EA_EINVAL, "stream must be < 2^24");
+    void *scr;
+    int32_t *d_slot;
+    const size_t bytes = (size_t)n * 2 * sizeof(uint32_t);
+    int rc = upload_slots(ctx, chains, n, bytes, &scr, &d_slot);
+    if (rc) return rc;
+    uint32_t *d_rid = (uint32_t *)scr, *d_stream = d_rid + n;
+    EA_CUDA(cudaMemcpyAsync(d_rid, rids, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    EA_CUDA(cudaMemcpyAsync(d_stream, streams, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    EA_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    EA_CUDA(launch_reset_lanes(ctx->d_tiles, ctx->dim, ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_lnW,
+                               ctx->d_hist, d_slot, d_rid, d_stream, n, ctx->key, ctx->d_err, ctx->stream));
+    EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW, ctx->d_thr,
+                            ctx->stream));
+    int herr = 0;
+    EA_CUDA(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    if ((rc = ctx_refresh_chains(ctx))) return rc;
+    if (herr) return fail(EA_ESTATE, "descent to E_top got stuck for a reset chain (left inactive)");
+    return EA_OK;
+}
+
+extern "C" int muca_update_weights_subset(ea_ctx *ctx, const int32_t *chains, int n) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (n < 0 || (n > 0 && !chains)) return fail(EA_EINVAL, "bad chain list");
+    if (n == 0) return EA_OK;
+    void *scr;
+    int32_t *d_slot;
+    int rc = upload_slots(ctx, chains, n, 0, &scr, &d_slot);
+    if (rc) return rc;
+    EA_CUDA(launch_update_weights_sel(ctx->d_tiles, ctx->d_slots, ctx->d_lnW, ctx->d_hist, d_slot, n, ctx->stream));
+    EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW, ctx->d_thr,
+                            ctx->stream));
     EA_CUDA(cudaStreamSynchronize(ctx->stream));
     return EA_OK;
 }

@@ -43,6 +43,7 @@ struct ea_ctx {
     // a8: launch configuration of the sweep kernel and the captured iteration graph
     int persistent = 0;               // 1: resident grid pulling tiles from a queue
     uint64_t sweeps_per_launch = 0;   // 0: all requested sweeps in one launch
+    int blocks_per_sm = 0;            // persistent grid: resident blocks per SM (0: occupancy limit)
     int n_sm = 0;
     int32_t *d_order = nullptr;       // tile ids, longest tiles first
     size_t order_cap = 0;

@@ -22,7 +22,7 @@ constexpr int kNoBottom = -1;  // b_g when no E_g is known yet: never reached
 
 struct TileDesc {
     int32_t dim, L, V, B;  // B = table rows per chain = largest b_top + 1 for this (dim, L)
-    int32_t n_active, pad0;
+    int32_t n_active, sweep_mul;  // sweep_mul: this tile runs n_sweeps * sweep_mul sweeps
     uint64_t w_base;       // element offset of lane 0's lnW / hist rows
     uint64_t spin_off;     // word offset of the tile's V spin words
     uint64_t bond_off;     // word offset of the tile's dim*V bond words
@@ -75,6 +75,12 @@ cudaError_t launch_update_weights(const TileDesc *d_tiles, int n_tiles, SlotStat
 cudaError_t launch_build_ensemble(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
                                   const uint8_t *d_sel, int kind, double alpha, double pole,
                                   double beta, double *d_lnW, cudaStream_t st);
+cudaError_t launch_reset_lanes(const TileDesc *d_tiles, int dim, SlotState *d_slots, uint32_t *d_spins,
+                               uint32_t *d_bonds, double *d_lnW, uint32_t *d_hist, const int32_t *d_slot_of,
+                               const uint32_t *d_rids, const uint32_t *d_streams, int n, PhiloxKey key,
+                               int *d_err, cudaStream_t st);
+cudaError_t launch_update_weights_sel(const TileDesc *d_tiles, SlotState *d_slots, double *d_lnW,
+                                      uint32_t *d_hist, const int32_t *d_slot_of, int n, cudaStream_t st);
 cudaError_t launch_reset_rt(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
                             const uint8_t *d_sel, cudaStream_t st);
 

@@ -154,10 +154,23 @@ __device__ __forceinline__ double ln_profile(int kind, double alpha, double pole
 }
 
 // one block per chain; threads over bins
+__device__ void update_weights_one(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                   double *__restrict__ lnW, uint32_t *__restrict__ hist, int slot);
+
 __global__ void update_weights_kernel(const TileDesc *__restrict__ tiles,
                                       SlotState *__restrict__ slots, double *__restrict__ lnW,
                                       uint32_t *__restrict__ hist) {
-    const int slot = blockIdx.x;
+    update_weights_one(tiles, slots, lnW, hist, blockIdx.x);
+}
+
+__global__ void update_weights_sel_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                          double *__restrict__ lnW, uint32_t *__restrict__ hist,
+                                          const int32_t *__restrict__ slot_of) {
+    update_weights_one(tiles, slots, lnW, hist, slot_of[blockIdx.x]);
+}
+
+__device__ void update_weights_one(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                   double *__restrict__ lnW, uint32_t *__restrict__ hist, int slot) {
     const TileDesc td = tiles[slot / kTile];
     const int lane = slot % kTile;
     SlotState ss = slots[slot];
@@ -287,6 +300,102 @@ __global__ void enforce_walls_kernel(const TileDesc *__restrict__ tiles,
     }
 }
 
+// Re-initialises single chains in place (serving: a freed lane takes a new job).  One warp
+// per chain; only the chain's own bit of each tile word changes (atomic and / or), so the
+// other lanes of the tile are untouched.  Couplings and spins come from the chain's new
+// (rid, stream) exactly as in init_kernel, then lane 0 descends to E <= E_top.
+template <int DIM>
+__global__ void reset_lane_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                  uint32_t *__restrict__ spins, uint32_t *__restrict__ bonds,
+                                  double *__restrict__ lnW, uint32_t *__restrict__ hist,
+                                  const int32_t *__restrict__ slot_of, const uint32_t *__restrict__ rids,
+                                  const uint32_t *__restrict__ streams, PhiloxKey key, int *__restrict__ err) {
+    const int slot = slot_of[blockIdx.x];
+    const int tile = slot / kTile, who = slot % kTile, lane = threadIdx.x;
+    const TileDesc td = tiles[tile];
+    const int L = td.L, V = td.V, nb = DIM * V;
+    const uint32_t rid = rids[blockIdx.x], stream = streams[blockIdx.x];
+    const uint32_t bit = 1u << who;
+    uint32_t *sp = spins + td.spin_off;
+    uint32_t *bd = bonds + td.bond_off;
+    int negatives = 0;
+    for (int j0 = 4 * lane; j0 < nb; j0 += 128) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), 0u, rid, 3u), key);
+        for (int jj = 0; jj < 4 && j0 + jj < nb; ++jj) {
+            const bool neg = (uint4_get(w, jj) >> 31) != 0;
+            negatives += neg;
+            if (neg) atomicOr(&bd[j0 + jj], bit);
+            else atomicAnd(&bd[j0 + jj], ~bit);
+        }
+    }
+    for (int i0 = 4 * lane; i0 < V; i0 += 128) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), 0u, rid, 2u | (stream << 8)), key);
+        for (int jj = 0; jj < 4 && i0 + jj < V; ++jj) {
+            if ((uint4_get(w, jj) >> 31) != 0) atomicOr(&sp[i0 + jj], bit);
+            else atomicAnd(&sp[i0 + jj], ~bit);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) negatives += __shfl_xor_sync(0xFFFFFFFFu, negatives, off);
+    __syncwarp();
+    __threadfence_block();
+    double *w = lnW + td.w_base + (uint64_t)who * td.B;
+    uint32_t *h = hist + td.w_base + (uint64_t)who * td.B;
+    for (int b = lane; b < td.B; b += 32) { w[b] = 0.0; h[b] = 0u; }
+    if (lane != 0) return;
+    auto spin = [&](int i) { return (sp[i] >> who) & 1u; };
+    auto unsat_at = [&](int i) {
+        int n = 0;
+        for (int d = 0; d < DIM; ++d) {
+            const int jp = nbr<DIM>(i, L, d, +1), jm = nbr<DIM>(i, L, d, -1);
+            n += (int)(spin(i) ^ spin(jp) ^ ((bd[i * DIM + d] >> who) & 1u));
+            n += (int)(spin(i) ^ spin(jm) ^ ((bd[jm * DIM + d] >> who) & 1u));
+        }
+        return n;
+    };
+    int u = 0;
+    for (int i = 0; i < V; ++i)
+        for (int d = 0; d < DIM; ++d)
+            u += (int)(spin(i) ^ spin(nbr<DIM>(i, L, d, +1)) ^ ((bd[i * DIM + d] >> who) & 1u));
+    int E = 2 * u - nb;
+    const int parity = negatives & 1;
+    const int btop = top_bin(nb, parity);
+    const int etop = energy_of_bin(nb, parity, btop);
+    bool stuck = false;
+    while (E > etop && !stuck) {
+        bool flipped = false;
+        for (int i = 0; i < V && E > etop; ++i) {
+            const int dE = 2 * (2 * DIM) - 4 * unsat_at(i);
+            if (dE < 0) { atomicXor(&sp[i], bit); E += dE; flipped = true; }
+        }
+        if (E > etop && !flipped) stuck = true;
+    }
+    SlotState ss = slots[slot];
+    ss.rid = rid;
+    ss.stream = stream;
+    ss.parity = parity;
+    ss.b_top = btop;
+    ss.b = stuck ? 0 : bin_of_energy(nb, E);
+    ss.b_min = ss.b;
+    ss.b_g = kNoBottom;
+    ss.e_g = -(1 << 30);
+    ss.phase = 0;
+    ss.n_rt = 0;
+    ss.t_first = -1;
+    ss.t_last = -1;
+    ss.t = 0;
+    ss.requeue = 0;
+    ss.kind = 0;
+    ss.active = stuck ? 0 : 1;
+    slots[slot] = ss;
+    if (stuck) atomicExch(err, 1);
+}
+
+// weight update of selected chains only (serving: jobs reach iteration boundaries at
+// different times)
+__global__ void update_weights_sel_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                          double *__restrict__ lnW, uint32_t *__restrict__ hist,
+                                          const int32_t *__restrict__ slot_of);
+
 __global__ void reset_rt_kernel(const TileDesc *__restrict__ tiles, int n_slots,
                                 SlotState *__restrict__ slots, const uint8_t *__restrict__ sel) {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,6 +455,27 @@ cudaError_t launch_build_ensemble(const TileDesc *d_tiles, int n_tiles, SlotStat
     const int n_slots = n_tiles * kTile;
     build_ensemble_kernel<<<(n_slots + 127) / 128, 128, 0, st>>>(d_tiles, n_slots, d_slots, d_sel,
                                                                  kind, alpha, pole, beta, d_lnW);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_lanes(const TileDesc *d_tiles, int dim, SlotState *d_slots, uint32_t *d_spins,
+                               uint32_t *d_bonds, double *d_lnW, uint32_t *d_hist, const int32_t *d_slot_of,
+                               const uint32_t *d_rids, const uint32_t *d_streams, int n, PhiloxKey key,
+                               int *d_err, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (dim == 3)
+        reset_lane_kernel<3><<<n, 32, 0, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_lnW, d_hist, d_slot_of, d_rids,
+                                               d_streams, key, d_err);
+    else
+        reset_lane_kernel<2><<<n, 32, 0, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_lnW, d_hist, d_slot_of, d_rids,
+                                               d_streams, key, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_weights_sel(const TileDesc *d_tiles, SlotState *d_slots, double *d_lnW,
+                                      uint32_t *d_hist, const int32_t *d_slot_of, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    update_weights_sel_kernel<<<n, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_hist, d_slot_of);
     return cudaGetLastError();
 }
 

@@ -353,9 +353,10 @@ __device__ __forceinline__ void sweep_one(const TileDesc *__restrict__ tiles, in
                                           uint32_t *hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
                                           unsigned char *smem_raw) {
     const TileDesc td = tiles[tile];
+    const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CASE(LL)                                                                      \
     case LL:                                                                               \
-        sweep_tile<DIM, LL>(td, tile, slots, spins, bonds, thr, hist, n_sweeps, key, count_rt, \
+        sweep_tile<DIM, LL>(td, tile, slots, spins, bonds, thr, hist, n_tile, key, count_rt, \
                             smem_raw);                                                     \
         break;
     switch (td.L) {

@@ -69,7 +69,10 @@ SIGNATURES = {
     "get_roundtrips": (_i, [P, _i, _i, P, _i]),
     "get_state": (_i, [P, _i, _i, P, _i, P, P]),
     "ea_synchronize": (_i, [P]),
-    "muca_set_launch": (_i, [P, _i, _u64]),
+    "muca_set_launch": (_i, [P, _i, _u64, _i]),
+    "ea_reset_chains": (_i, [P, P, _i, P, P]),
+    "muca_set_sweep_multiplier": (_i, [P, _i, _i]),
+    "muca_update_weights_subset": (_i, [P, P, _i]),
     "ea_graph_capture": (_i, [P, _i, _u64, _i, _i]),
     "ea_graph_launch": (_i, [P, _i]),
     "ea_graph_release": (_i, [P]),
@@ -232,9 +235,24 @@ class Context:
     def synchronize(self):
         check(lib().ea_synchronize(self._h))
 
+    # a9: serving support
+    def reset_chains(self, chains, rids, streams):
+        c = np.ascontiguousarray(chains, dtype=np.int32)
+        r = np.ascontiguousarray(rids, dtype=np.uint32)
+        s = np.ascontiguousarray(streams, dtype=np.uint32)
+        check(lib().ea_reset_chains(self._h, _p(c), c.shape[0], _p(r), _p(s)))
+
+    def set_sweep_multiplier(self, L: int, multiplier: int):
+        check(lib().muca_set_sweep_multiplier(self._h, L, multiplier))
+
+    def update_weights_subset(self, chains):
+        c = np.ascontiguousarray(chains, dtype=np.int32)
+        check(lib().muca_update_weights_subset(self._h, _p(c), c.shape[0]))
+
     # a8: launch configuration and the captured iteration graph
-    def set_launch(self, persistent: bool = False, sweeps_per_launch: int = 0):
-        check(lib().muca_set_launch(self._h, int(persistent), sweeps_per_launch))
+    def set_launch(self, persistent: bool = False, sweeps_per_launch: int = 0,
+                   blocks_per_sm: int = 0):
+        check(lib().muca_set_launch(self._h, int(persistent), sweeps_per_launch, blocks_per_sm))
 
     def graph_capture(self, n_iter: int, sweeps_per_iter: int, count_roundtrips: bool = False,
                       update_weights: bool = True):

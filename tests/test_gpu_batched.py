@@ -53,7 +53,7 @@ def test_persistent_and_split_launches_match_plain(eamc):
     _run(ref, 3, 40)
     for persistent, spl in ((True, 0), (False, 7), (True, 13)):
         ctx = _mixed(eamc)
-        ctx.set_launch(persistent, spl)
+        ctx.set_launch(persistent, spl, 2 if persistent else 0)
         _run(ctx, 3, 40)
         _same(_state(ref), _state(ctx))
 
