@@ -38,6 +38,10 @@ UNIT = "attempts/ns"
 # plus extraction) + 3 (threshold fetch and compare) + 2 (flip and energy update)
 # + 3 (lowest energy and round-trip check)
 ALG_OPS_PER_ATTEMPT = 21.5
+# PT, per site word of 32 lattices (32 attempts): 12 word loads + 14 bit ops for the
+# unsatisfied counts + 4 for the classes, about 8 compared bit planes (2 Philox4x32-10 calls of
+# 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
+PT_ALG_OPS = 4.7
 
 
 def parse():
@@ -49,6 +53,10 @@ def parse():
     ap.add_argument("--sweeps-per-step", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
+    ap.add_argument("--only", choices=["pt", "uneven", "serving"], default=None,
+                    help="run one secondary workload alone and print its record (profiling)")
+    ap.add_argument("--pt-sweeps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -274,6 +282,94 @@ def plain_form(eamc, stream, S: int):
             "what": f"one realization per launch, {S} sweeps, L={W.L}"}
 
 
+def bench_pt(S: int = 200):
+    """PT workload: L=8, 1024 realizations x 32 temperatures (geometric beta in [0.2, 3])."""
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    from paper_2011_08560_gb300.workloads import PT, geometric_betas
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=PT["seed"], device=0, stream=stream.cuda_stream)
+    betas = geometric_betas(PT["M"], PT["beta_min"], PT["beta_max"])
+    ctx.pt_init(PT["dim"], PT["L"], PT["n_real"], betas)
+    ctx.pt_run(20)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.pt_run(S)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    attempts = PT["n_real"] * PT["M"] * PT["L"] ** 3 * S
+    swaps = ctx.pt_swap_counts()
+    ctx.close()
+    return {"workload": "PT: 3D L=8, 1024 realizations x 32 temperatures, beta geometric in [0.2, 3]",
+            "sweeps": S, "ms": ms, "attempts_per_ns": attempts / (ms * 1e6),
+            "alg_ops_per_attempt": PT_ALG_OPS, "achieved_Tops": attempts * PT_ALG_OPS / (ms * 1e9),
+            "swap_acceptance_mean": float(swaps.sum() / max(1, (PT["M"] - 1) * PT["n_real"] * (20 + S) / 2))}
+
+
+def bench_uneven(S: int = 100, iters: int = 3):
+    """Uneven batch: 4096 realizations, L uniform over {4,6,8,10,12} (round robin by id), each
+    as a power-law, a flat and a 1/k chain, in one persistent launch per step; the
+    weight-iteration loop is a captured CUDA graph."""
+    import torch
+
+    from paper_2011_08560_gb300 import autotune, eamc
+    from paper_2011_08560_gb300.workloads import UNEVEN
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=UNEVEN["seed"], device=0, stream=stream.cuda_stream)
+    Ls = UNEVEN["Ls"]
+    groups, one_over_k = [], []
+    for kind_idx, kind in enumerate((eamc.EA_POWERLAW, eamc.EA_FLAT, eamc.EA_ONE_OVER_K)):
+        for L in Ls:
+            # realization ids with L = Ls[id % 5] are a contiguous block after sorting by L
+            n = sum(1 for r in range(UNEVEN["n_real"]) if Ls[r % len(Ls)] == L)
+            first = ctx.init_disorder(3, L, n, rid0=Ls.index(L) * UNEVEN["n_real"], stream=kind_idx)
+            ctx.set_ensemble(first, n, eamc.EA_POWERLAW if kind == eamc.EA_POWERLAW else eamc.EA_FLAT)
+            if kind == eamc.EA_ONE_OVER_K:
+                one_over_k.append((first, n))
+            groups.append((3, L, n))
+    best = autotune.apply(ctx, groups, sweeps=20)
+    # one iteration step, then the 1/k chains take 1/k weights built from their estimate
+    ctx.run_sweeps(S, count_roundtrips=False)
+    ctx.update_weights()
+    for first, n in one_over_k:
+        ctx.build_ensemble(first, n, eamc.EA_ONE_OVER_K)
+    attempts_per_sweep = sum(n * L ** 3 for _, L, n in groups)
+    ctx.graph_capture(n_iter=iters, sweeps_per_iter=S, count_roundtrips=True, update_weights=True)
+    ctx.graph_launch(1)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.graph_launch(1)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"workload": "4096 realizations, L in {4,6,8,10,12} round robin, x3 ensembles "
+                        "(power law, flat, 1/k), graph-captured iteration loop",
+            "chains": sum(n for _, _, n in groups), "graph": f"{iters} x ({S} sweeps + weight update)",
+            "ms": ms, "attempts_per_ns": attempts_per_sweep * S * iters / (ms * 1e6), "launch": best}
+
+
+def bench_serving(window_s: float = 4.0, drain_s: float = 20.0):
+    """Serving: Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12}, round-trip
+    targets log-uniform in [10, 1000]; device-resident state, memory-based admission."""
+    from paper_2011_08560_gb300 import serve
+    from paper_2011_08560_gb300.workloads import SERVING
+    jobs = serve.poisson_jobs(SERVING["rate_hz"], window_s, SERVING["Ls"], SERVING["rt_min"],
+                              SERVING["rt_max"], seed=SERVING["seed"], iter_steps=4,
+                              ticks_per_step=8, max_prod_ticks=400)
+    server = serve.Server(seed=SERVING["seed"], Ls=SERVING["Ls"], base_sweeps=2,
+                          mem_budget=4 << 30)
+    stats = serve.run_poisson(server, jobs, duration_s=window_s, drain_s=drain_s)
+    server.close()
+    stats["workload"] = (f"Poisson {SERVING['rate_hz']:.0f} jobs/s for {window_s:.0f} s, L in 4..12, "
+                         f"round-trip targets log-uniform [10, 1000], sweep caps (censored jobs counted)")
+    return stats
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -308,6 +404,10 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.only:
+        fn = {"pt": lambda: bench_pt(args.pt_sweeps), "uneven": bench_uneven, "serving": bench_serving}
+        print(json.dumps({"only": args.only, **fn[args.only]()}))
+        return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
@@ -315,6 +415,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()      # spawn pool before the first CUDA call
     r = run_gpu(args, rank, world)
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = {"pt": bench_pt(), "uneven": bench_uneven(), "serving": bench_serving()}
     if rank != 0:
         if world > 1:
             import torch
@@ -339,6 +442,7 @@ def main():
                      "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock"},
         "clocks": r["clocks"],
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "extras": extras,
     }
     print(json.dumps(line))
     if world > 1:
