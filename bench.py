@@ -42,6 +42,9 @@ ALG_OPS_PER_ATTEMPT = 21.5
 # unsatisfied counts + 4 for the classes, about 8 compared bit planes (2 Philox4x32-10 calls of
 # 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
 PT_ALG_OPS = 4.7
+# dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch of the headline workload
+# (ncu, profiles/muca_sweep_L6_2048chains.md)
+SWEEP_TRAFFIC_BYTES = 11.68e6
 
 
 def parse():
@@ -436,7 +439,9 @@ def main():
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "achieved": r["achieved_ops"] / 1e12,
                      "peak": r["alu_peak"] / 1e12, "unit": "Tops/s",
-                     "frac": r["achieved_ops"] / r["alu_peak"], "traffic": None,
+                     "frac": r["achieved_ops"] / r["alu_peak"], "traffic": SWEEP_TRAFFIC_BYTES,
+                     "traffic_source": "profiles/muca_sweep_L6_2048chains.md (dram read+write of one "
+                                       "launch; one-time staging of the tables, independent of sweeps)",
                      "kernel": "muca_sweep_kernel<3>",
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock"},
