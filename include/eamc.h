@@ -238,6 +238,34 @@ int pt_get_roundtrips(ea_ctx *ctx, ea_pt_stats *out, int reset);
 /* Accepted exchanges per slot pair (k, k+1), summed over realizations: uint64[M-1]. */
 int pt_get_swap_counts(ea_ctx *ctx, uint64_t *out);
 
+/* ------------------------------------------------------------------ no allocation
+ * The paper has no counterpart to this entry point: it serves callers that cannot allocate
+ * device memory (code inside another framework's memory pool or under a fixed device-memory
+ * budget, plugins that may only touch the buffers they are given).  It runs n_sweeps MUCA
+ * sweeps (the muca_run_sweeps kernel, without round-trip counting) on n chains of linear size
+ * L without a context and without allocating anything: no cudaMalloc, no cudaFree, no
+ * allocating library call.  Its working memory is one static device array of 4 MiB in the
+ * library, which every GPU that loads the library holds until the process exits; at most
+ * 256 chains, and fewer at large L (L=8: 256, L=12: about 90) -- larger requests return
+ * EA_EINVAL.  The first call on a device looks up the array's device address and should come
+ * before any stream capture.  Calls share the array: calls that overlap on the GPU race.
+ *
+ * All buffers are DEVICE pointers owned by the caller, for chains c = 0..n-1:
+ *   rid[c], stream_id[c]       uint32 realization id and random stream (as ea_init_disorder)
+ *   couplings[c][dim*V]        int8 +-1 (in)
+ *   spins[c][V]                int8 +-1 (in / out); every chain must start with E <= E_top
+ *   energies[c]                int32 (out)
+ *   thr[c][B][8]               uint32 acceptance thresholds (in), B = (dim*V/2 >> 1) + 1
+ *   hist[c][B]                 uint32 histogram (in / out, accumulated)
+ * t0 is the sweep index of the first sweep (random words are keyed by it, so two calls with
+ * t0 and t0 + n_sweeps continue one trajectory).  Work is queued on cuda_stream (may be NULL)
+ * and the call returns after it completes.  EA_EINVAL if a chain starts above E_top (the
+ * chain is then left unchanged). */
+int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, const uint32_t *rid,
+                            const uint32_t *stream_id, const int8_t *couplings, int8_t *spins,
+                            int32_t *energies, const uint32_t *thr, uint32_t *hist, uint64_t t0,
+                            uint64_t n_sweeps, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ SIGNATURES = {
     "ea_graph_capture": (_i, [P, _i, _u64, _i, _i]),
     "ea_graph_launch": (_i, [P, _i]),
     "ea_graph_release": (_i, [P]),
+    "muca_run_sweeps_noalloc": (_i, [_i, _i, _i, _u64, P, P, P, P, P, P, P, _u64, _u64, P]),
     "pt_init": (_i, [P, _i, _i, _i, _u32, _i, P, P]),
     "pt_set_rt_bounds": (_i, [P, P, P]),
     "pt_run": (_i, [P, _u64, _i]),
