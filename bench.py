@@ -363,8 +363,8 @@ def bench_serving(window_s: float = 4.0, drain_s: float = 20.0):
     from paper_2011_08560_gb300.workloads import SERVING
     jobs = serve.poisson_jobs(SERVING["rate_hz"], window_s, SERVING["Ls"], SERVING["rt_min"],
                               SERVING["rt_max"], seed=SERVING["seed"], iter_steps=4,
-                              ticks_per_step=8, max_prod_ticks=400)
-    server = serve.Server(seed=SERVING["seed"], Ls=SERVING["Ls"], base_sweeps=2,
+                              ticks_per_step=4, max_prod_ticks=200)
+    server = serve.Server(seed=SERVING["seed"], Ls=SERVING["Ls"], base_sweeps=16,
                           mem_budget=4 << 30)
     stats = serve.run_poisson(server, jobs, duration_s=window_s, drain_s=drain_s)
     server.close()

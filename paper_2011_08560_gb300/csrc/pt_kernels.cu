@@ -414,7 +414,10 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(p->n_groups * p->cs);
-    cfg.blockDim = dim3(256);
+    // up to one thread per site of one colour of the CTA's slots (at most 256, at least 2
+    // warps); 512-thread blocks measured slower (barrier cost, register cap)
+    const int items = a.spc * (G::V / 2);
+    cfg.blockDim = dim3(std::min(256, std::max(64, (items + 31) / 32 * 32)));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
