@@ -152,11 +152,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def shard_rid0(rank: int, n_per_rank: int) -> int:
+    """Realizations of a rank: ids rank*n .. rank*n + n - 1 (disjoint; no data-path exchange)."""
+    return rank * n_per_rank
+
+
+def reduce_max_ms(t_ms: float, world: int, device=None) -> float:
+    """The job's time is the slowest rank's (max over ranks of the timed interval)."""
+    if world <= 1:
+        return t_ms
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_context(eamc, rank: int, stream_ptr: int):
     W = HEADLINE
     ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
     n = W.n_real
-    rid0 = rank * n
+    rid0 = shard_rid0(rank, n)
     ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=0)          # flat MUCA chains
     ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=1)          # power-law MUCA chains
     ctx.set_ensemble(0, n, eamc.EA_FLAT)
@@ -219,9 +234,7 @@ def run_gpu(args, rank, world):
     kern_ms = [s.elapsed_time(e) for s, e in zip(k_starts, k_ends)]
     t_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
+        t_ms = reduce_max_ms(t_ms, world, device="cuda")
         torch.distributed.barrier()
     rts = total_rt(ctx) - rt0
     value = world * attempts_per_step * args.steps / (t_ms * 1e6)

@@ -196,17 +196,31 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                 uint32_t und = up & valid;
                 const int k = k0 + ks;
                 const uint32_t T0 = Th[ks * 8 + 0], T1 = Th[ks * 8 + 1], T2 = Th[ks * 8 + 2];
+                // the 8 most significant planes come from two independent Philox calls and are
+                // compared without branches; planes 8..31 are drawn only while a bit is still
+                // undecided (about 2^-8 per uphill bit)
+                const uint32_t c2 = (uint32_t)g + (a.rid0 >> 5), c3 = 4u | ((uint32_t)k << 8);
+                const uint4 wa = philox4x32_10(make_uint4((uint32_t)(8 * i), tt, c2, c3), a.key);
+                const uint4 wb = philox4x32_10(make_uint4((uint32_t)(8 * i + 1), tt, c2, c3), a.key);
+                const uint32_t Rm[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int sh = 31 - m;
+                    const uint32_t Tm = (C[0] & (0u - ((T0 >> sh) & 1u))) | (C[1] & (0u - ((T1 >> sh) & 1u))) |
+                                        (C[2] & (0u - ((T2 >> sh) & 1u)));
+                    acc |= und & ~Rm[m] & Tm;  // r bit 0, threshold bit 1: r < threshold
+                    und &= ~(Rm[m] ^ Tm);      // equal bits: still undecided
+                }
                 uint4 w4 = make_uint4(0, 0, 0, 0);
-                for (int m = 0; m < 32 && und; ++m) {
+                for (int m = 8; m < 32 && und; ++m) {
                     if ((m & 3) == 0)
-                        w4 = philox4x32_10(make_uint4((uint32_t)(8 * i + (m >> 2)), tt, (uint32_t)g + (a.rid0 >> 5),
-                                                      4u | ((uint32_t)k << 8)), a.key);
+                        w4 = philox4x32_10(make_uint4((uint32_t)(8 * i + (m >> 2)), tt, c2, c3), a.key);
                     const uint32_t R = uint4_get(w4, m & 3);
                     const int sh = 31 - m;
                     const uint32_t Tm = (C[0] & (0u - ((T0 >> sh) & 1u))) | (C[1] & (0u - ((T1 >> sh) & 1u))) |
                                         (C[2] & (0u - ((T2 >> sh) & 1u)));
-                    acc |= und & ~R & Tm;   // r bit 0, threshold bit 1: r < threshold
-                    und &= ~(R ^ Tm);       // equal bits: still undecided
+                    acc |= und & ~R & Tm;
+                    und &= ~(R ^ Tm);
                 }
                 Sk[i] = si ^ (acc & valid);
             }
@@ -508,7 +522,7 @@ extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, i
     p->dmax = p->nb / 2;
     p->betas.assign(betas, betas + M);
     p->cs = 1;
-    for (int c : {8, 4, 2})
+    for (int c : {8, 4, 2})  // 16-CTA clusters measured slower
         if (M % c == 0) { p->cs = c; break; }
     const size_t G = p->n_groups;
     auto alloc = [&](void **ptr, size_t bytes) -> int {
