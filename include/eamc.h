@@ -189,6 +189,16 @@ int get_roundtrips(ea_ctx *ctx, int chain0, int n, ea_rt_stats *out, int reset);
 int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stride, int32_t *E,
               uint64_t *t);
 
+/* Checkpoint / resume (not in the paper; random words are keyed by each chain's sweep
+ * counter, so a run resumed from a snapshot continues the identical trajectory).  size gives
+ * the snapshot's byte count; save writes the MUCA state of every chain (lattices, chain
+ * states, weights, histograms, thresholds, launch layout, seed) into a host buffer of at least
+ * that size; load restores it into a context that has no chains yet (PT state and the launch
+ * configuration are not part of a snapshot). */
+int ea_snapshot_size(ea_ctx *ctx, size_t *bytes);
+int ea_snapshot_save(ea_ctx *ctx, void *buf, size_t cap);
+int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size);
+
 /* Waits for all queued work of the context. */
 int ea_synchronize(ea_ctx *ctx);
 

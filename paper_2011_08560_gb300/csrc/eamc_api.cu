@@ -858,3 +858,130 @@ extern "C" int ea_synchronize(ea_ctx *ctx) {
     EA_CUDA(cudaGetLastError());
     return EA_OK;
 }
+
+// ------------------------------------------------------------------------------ snapshots
+namespace {
+constexpr uint64_t kSnapMagic = 0x45414d43534e4150ull;  // "EAMCSNAP"
+constexpr uint32_t kSnapVersion = 1;
+
+struct SnapHeader {
+    uint64_t magic;
+    uint32_t version, dim;
+    uint64_t seed, n_tiles, n_chains, spin_used, bond_used, w_used, max_t_host;
+    int32_t max_V, pad;
+    uint64_t sweep_smem;
+};
+
+template <class T>
+size_t put_vec(char *dst, const std::vector<T> &v) {
+    if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(T));
+    return v.size() * sizeof(T);
+}
+}  // namespace
+
+static size_t snapshot_bytes(const ea_ctx *ctx) {
+    const size_t nt = ctx->tiles.size(), nc = ctx->chain_slot.size();
+    return sizeof(SnapHeader) + nt * sizeof(TileDesc) + nc * (sizeof(int32_t) * 2 + sizeof(uint64_t)) +
+           nt * kTile * sizeof(SlotState) + (ctx->spin_used + ctx->bond_used) * sizeof(uint32_t) +
+           ctx->w_used * (sizeof(double) + sizeof(uint32_t) + 8 * sizeof(uint32_t));
+}
+
+extern "C" int ea_snapshot_size(ea_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return fail(EA_EINVAL, "null argument");
+    *bytes = snapshot_bytes(ctx);
+    return EA_OK;
+}
+
+extern "C" int ea_snapshot_save(ea_ctx *ctx, void *buf, size_t cap) {
+    if (!ctx || !buf) return fail(EA_EINVAL, "null argument");
+    const size_t need = snapshot_bytes(ctx);
+    if (cap < need) return fail(EA_EINVAL, "snapshot needs %zu bytes, buffer has %zu", need, cap);
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    char *p = (char *)buf;
+    SnapHeader h;
+    std::memset(&h, 0, sizeof h);
+    h.magic = kSnapMagic;
+    h.version = kSnapVersion;
+    h.dim = (uint32_t)ctx->dim;
+    h.seed = ctx->seed;
+    h.n_tiles = ctx->tiles.size();
+    h.n_chains = ctx->chain_slot.size();
+    h.spin_used = ctx->spin_used;
+    h.bond_used = ctx->bond_used;
+    h.w_used = ctx->w_used;
+    h.max_t_host = ctx->max_t_host;
+    h.max_V = ctx->max_V;
+    h.sweep_smem = ctx->sweep_smem;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    p += put_vec(p, ctx->tiles);  // host mirror (sweep multipliers included)
+    p += put_vec(p, ctx->chain_slot);
+    p += put_vec(p, ctx->chain_woff);
+    p += put_vec(p, ctx->chain_btop);
+    auto dev = [&](const void *src, size_t bytes) -> int {
+        if (bytes) EA_CUDA(cudaMemcpy(p, src, bytes, cudaMemcpyDeviceToHost));
+        p += bytes;
+        return EA_OK;
+    };
+    int rc;
+    if ((rc = dev(ctx->d_slots, h.n_tiles * kTile * sizeof(SlotState))) ||
+        (rc = dev(ctx->d_spins, h.spin_used * 4)) || (rc = dev(ctx->d_bonds, h.bond_used * 4)) ||
+        (rc = dev(ctx->d_lnW, h.w_used * 8)) || (rc = dev(ctx->d_hist, h.w_used * 4)) ||
+        (rc = dev(ctx->d_thr, h.w_used * 8 * 4)))
+        return rc;
+    return EA_OK;
+}
+
+extern "C" int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size) {
+    if (!ctx || !buf) return fail(EA_EINVAL, "null argument");
+    if (!ctx->tiles.empty()) return fail(EA_ESTATE, "a snapshot loads into a context without chains");
+    if (size < sizeof(SnapHeader)) return fail(EA_EINVAL, "snapshot too short");
+    SnapHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != kSnapMagic || h.version != kSnapVersion) return fail(EA_EINVAL, "not an eamc snapshot");
+    const char *p = (const char *)buf + sizeof h;
+    std::vector<TileDesc> tiles(h.n_tiles);
+    std::vector<int32_t> cslot(h.n_chains), cbtop(h.n_chains);
+    std::vector<uint64_t> cwoff(h.n_chains);
+    const size_t need = sizeof h + h.n_tiles * sizeof(TileDesc) + h.n_chains * 16 + h.n_tiles * kTile * sizeof(SlotState) +
+                        (h.spin_used + h.bond_used) * 4 + h.w_used * (8 + 4 + 32);
+    if (size < need) return fail(EA_EINVAL, "snapshot truncated (%zu of %zu bytes)", size, need);
+    std::memcpy(tiles.data(), p, h.n_tiles * sizeof(TileDesc)); p += h.n_tiles * sizeof(TileDesc);
+    std::memcpy(cslot.data(), p, h.n_chains * 4); p += h.n_chains * 4;
+    std::memcpy(cwoff.data(), p, h.n_chains * 8); p += h.n_chains * 8;
+    std::memcpy(cbtop.data(), p, h.n_chains * 4); p += h.n_chains * 4;
+    int rc;
+    if ((rc = grow(&ctx->d_tiles, &ctx->tiles_cap, 0, h.n_tiles, ctx->stream)) ||
+        (rc = grow(&ctx->d_slots, &ctx->slots_cap, 0, h.n_tiles * kTile, ctx->stream)) ||
+        (rc = grow(&ctx->d_spins, &ctx->spins_cap, 0, h.spin_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_bonds, &ctx->bonds_cap, 0, h.bond_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_lnW, &ctx->lnW_cap, 0, h.w_used, ctx->stream)) ||
+        (rc = grow(&ctx->d_hist, &ctx->hist_cap, 0, h.w_used, ctx->stream)) ||
+        (rc = grow_thr(ctx, h.w_used * 8)))
+        return rc;
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    auto dev = [&](void *dst, size_t bytes) -> int {
+        if (bytes) EA_CUDA(cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice));
+        p += bytes;
+        return EA_OK;
+    };
+    EA_CUDA(cudaMemcpy(ctx->d_tiles, tiles.data(), h.n_tiles * sizeof(TileDesc), cudaMemcpyHostToDevice));
+    if ((rc = dev(ctx->d_slots, h.n_tiles * kTile * sizeof(SlotState))) || (rc = dev(ctx->d_spins, h.spin_used * 4)) ||
+        (rc = dev(ctx->d_bonds, h.bond_used * 4)) || (rc = dev(ctx->d_lnW, h.w_used * 8)) ||
+        (rc = dev(ctx->d_hist, h.w_used * 4)) || (rc = dev(ctx->d_thr, h.w_used * 8 * 4)))
+        return rc;
+    ctx->dim = (int)h.dim;
+    ctx->seed = h.seed;
+    ctx->key = PhiloxKey{(uint32_t)h.seed, (uint32_t)(h.seed >> 32)};
+    ctx->tiles = tiles;
+    ctx->chain_slot = cslot;
+    ctx->chain_woff = cwoff;
+    ctx->chain_btop = cbtop;
+    ctx->spin_used = h.spin_used;
+    ctx->bond_used = h.bond_used;
+    ctx->w_used = h.w_used;
+    ctx->max_t_host = h.max_t_host;
+    ctx->max_V = h.max_V;
+    ctx->sweep_smem = h.sweep_smem;
+    return ctx_rebuild_order(ctx);
+}

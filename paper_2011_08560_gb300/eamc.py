@@ -69,6 +69,9 @@ SIGNATURES = {
     "get_roundtrips": (_i, [P, _i, _i, P, _i]),
     "get_state": (_i, [P, _i, _i, P, _i, P, P]),
     "ea_synchronize": (_i, [P]),
+    "ea_snapshot_size": (_i, [P, P]),
+    "ea_snapshot_save": (_i, [P, P, ctypes.c_size_t]),
+    "ea_snapshot_load": (_i, [P, P, ctypes.c_size_t]),
     "muca_set_launch": (_i, [P, _i, _u64, _i]),
     "ea_reset_chains": (_i, [P, P, _i, P, P]),
     "muca_set_sweep_multiplier": (_i, [P, _i, _i]),
@@ -235,6 +238,18 @@ class Context:
 
     def synchronize(self):
         check(lib().ea_synchronize(self._h))
+
+    # checkpoint / resume
+    def snapshot(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        check(lib().ea_snapshot_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(lib().ea_snapshot_save(self._h, buf, n.value))
+        return buf.raw
+
+    def restore(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        check(lib().ea_snapshot_load(self._h, buf, len(data)))
 
     # a9: serving support
     def reset_chains(self, chains, rids, streams):

@@ -92,3 +92,21 @@ def test_graph_replay_matches_direct_calls(eamc):
     ctx.graph_release()
     with pytest.raises(eamc.EamcError):
         ctx.graph_launch(1)
+
+
+def test_snapshot_resume_is_bit_exact(eamc):
+    """Run 2S sweeps straight vs S, snapshot, restore into a new context, S more."""
+    straight = _mixed(eamc)
+    _run(straight, 2, 30)
+    first = _mixed(eamc)
+    _run(first, 1, 30)
+    blob = first.snapshot()
+    resumed = eamc.Context(seed=999)          # the seed comes from the snapshot
+    resumed.restore(blob)
+    assert resumed.num_chains() == first.num_chains()
+    _run(resumed, 1, 30)
+    _same(_state(straight), _state(resumed))
+    with pytest.raises(eamc.EamcError):
+        resumed.restore(blob)                 # only into a context without chains
+    with pytest.raises(eamc.EamcError):
+        eamc.Context(seed=1).restore(blob[:100])
