@@ -12,6 +12,7 @@ What each function follows (Mueller, Schnabel, Janke, arXiv:2011.08560):
   quantize ................... Eq. "muca": P_acc = min(1, W(E_new)/W(E_old)) as a u32 threshold
   ln_profile ................. Eq. "power_law" (normalised to 1 at E = 0)
   update_weights ............. Sec. II, the iterative weight procedure (W <- W P_SH / H)
+  update_weights_berg ........ Sec. II / Janke 2003: Berg's accumulated error-weighted recursion
   build_weights .............. Eq. "muca-weights", nonflat weight, Eq. "1/k", canonical
   pt_tables / pt_sweeps ...... Sec. II, parallel tempering and Eq. "temperatureexchange"
   round trips ................ Sec. III (top -> E_g -> top, times in sweeps)
@@ -86,6 +87,7 @@ def lib():
             "or_quantize": (None, [i32, i32, P, P]),
             "or_ln_profile": (f64, [i32, f64, f64, i32, i32]),
             "or_update_weights": (None, [i32, i32, i32, i32, i32, f64, f64, i32, P, P]),
+            "or_update_weights_berg": (None, [i32, i32, i32, i32, i32, f64, f64, i32, P, P, P, P]),
             "or_build_weights": (None, [i32, i32, i32, i32, i32, f64, f64, f64, i32, P, P]),
             "or_pt_tables": (None, [i32, i32, P, i32, P, P]),
             "or_pt_sweeps": (i32, [i32, i32, u64, u32, i32, P, P, P, P, u64, u64, P, P, i32,
@@ -178,6 +180,22 @@ def update_weights(dim, L, par, kind, alpha, pole, e_g, lnW, hist) -> np.ndarray
     hist = np.ascontiguousarray(hist, dtype=np.uint32)
     lib().or_update_weights(dim, L, par, lnW.shape[0] - 1, kind, alpha, pole, e_g, _p(lnW),
                             _p(hist))
+    return lnW
+
+
+def berg_state(n_bins: int) -> np.ndarray:
+    """Accumulators of the Berg recursion: row 0 = D (weighted mean of the ln Omega
+    differences of neighbouring bins), row 1 = G (sum of their weights); both start at 0."""
+    return np.zeros((2, n_bins), dtype=np.float64)
+
+
+def update_weights_berg(dim, L, par, kind, alpha, pole, e_g, lnW, hist, acc) -> np.ndarray:
+    """One step of the accumulated recursion; `acc` (from berg_state) is updated in place."""
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64).copy()
+    hist = np.ascontiguousarray(hist, dtype=np.uint32)
+    assert acc.dtype == np.float64 and acc.flags.c_contiguous and acc.shape == (2, lnW.shape[0])
+    lib().or_update_weights_berg(dim, L, par, lnW.shape[0] - 1, kind, alpha, pole, e_g, _p(lnW),
+                                 _p(hist), _p(acc[0]), _p(acc[1]))
     return lnW
 
 

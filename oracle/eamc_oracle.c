@@ -261,6 +261,54 @@ void or_update_weights(int dim, int L, int parity, int b_top, int kind, double a
     for (int b = 0; b <= b_top; ++b) lnW[b] -= top;
 }
 
+/* Accumulated, error-weighted form of the weight iteration: Berg's multicanonical recursion
+ * (B. A. Berg, J. Stat. Phys. 82, 323 (1996); one of the iterative procedures of Janke 2003
+ * that Sec. II refers to), written for bins b of a shaped target P_SH.
+ *
+ * An iteration run with weights W_n and histogram H_n estimates, for a pair of neighbouring
+ * bins that were both visited,
+ *     s(b) = ln Omega(b+1) - ln Omega(b) = [ln H(b+1) - ln W_n(b+1)] - [ln H(b) - ln W_n(b)],
+ * with a Poisson variance of about 1/H(b) + 1/H(b+1).  D(b) is the mean of all iterations'
+ * estimates weighted by the inverse variances g = H(b) H(b+1) / (H(b) + H(b+1)), G(b) the sum
+ * of those weights (both start at 0).  The new weights follow from
+ *     ln W(b) - ln W(b+1) = ln P_SH(b) - ln P_SH(b+1) + D(b)       (target with the current E_g)
+ * for every pair with G(b) > 0; a pair never visited together takes the difference that the
+ * plain step (or_update_weights) gives it.  ln W is 0 at the top bin.  From D = G = 0 the
+ * first step equals the plain step.
+ *
+ * Weights that are constant over the range add no estimates: every move inside the range is
+ * then accepted with probability 1, so the sequential sweep is deterministic (it only flips
+ * back and forth) and its histogram is not the equilibrium one that the estimates assume. */
+void or_update_weights_berg(int dim, int L, int parity, int b_top, int kind, double alpha,
+                            double pole_dE, int e_g, double *lnW, const uint32_t *hist,
+                            double *D, double *G) {
+    double *diff = (double *)malloc(sizeof(double) * (size_t)(b_top > 0 ? b_top : 1));
+    int informative = 0;
+    for (int b = 0; b < b_top; ++b)
+        if (lnW[b] != lnW[b_top]) informative = 1;
+    for (int b = 0; b < b_top; ++b) {
+        double lp0 = or_ln_profile(kind, alpha, pole_dE, e_g, or_energy_of_bin(dim, L, parity, b));
+        double lp1 = or_ln_profile(kind, alpha, pole_dE, e_g, or_energy_of_bin(dim, L, parity, b + 1));
+        double h0 = (double)hist[b], h1 = (double)hist[b + 1];
+        if (informative && hist[b] > 0 && hist[b + 1] > 0) {
+            double s = (log(h1) - lnW[b + 1]) - (log(h0) - lnW[b]);
+            double g = h0 * h1 / (h0 + h1);
+            D[b] = (G[b] * D[b] + g * s) / (G[b] + g);
+            G[b] = G[b] + g;
+        }
+        if (G[b] > 0.0) {
+            diff[b] = lp0 - lp1 + D[b];
+        } else {
+            double a0 = lnW[b] + lp0 - log(h0 > 0.0 ? h0 : 1.0);
+            double a1 = lnW[b + 1] + lp1 - log(h1 > 0.0 ? h1 : 1.0);
+            diff[b] = a0 - a1;
+        }
+    }
+    lnW[b_top] = 0.0;
+    for (int b = b_top - 1; b >= 0; --b) lnW[b] = lnW[b + 1] + diff[b];
+    free(diff);
+}
+
 /* Weights of a target ensemble from a density-of-states estimate ln Omega(b):
  *   kind 0 flat       ln W = -ln Omega                           (Eq. "muca-weights")
  *   kind 1 power law  ln W = ln P_SH - ln Omega                  (nonflat weight)
