@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -33,7 +34,7 @@ from paper_2011_08560_gb300.workloads import HEADLINE  # noqa: E402
 
 METRIC = "spin-flip attempts/ns"
 UNIT = "attempts/ns"
-# algorithmic integer lane-operations per spin-flip attempt ("roofline"):
+# algorithmic integer lane-operations per spin-flip attempt:
 # 10 (quarter of a Philox4x32-10 call) + 3.5 (bit-sliced local field, 32 chains per word,
 # plus extraction) + 3 (threshold fetch and compare) + 2 (flip and energy update)
 # + 3 (lowest energy and round-trip check)
@@ -57,7 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
-    ap.add_argument("--only", choices=["pt", "uneven", "serving"], default=None,
+    ap.add_argument("--only", choices=["pt", "uneven", "serving", "recursion"], default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--pt-sweeps", type=int, default=200)
     return ap.parse_args()
@@ -108,7 +109,9 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = ROOT / "gpurun_out" / f"clocks_{os.getpid()}.csv"
+        # the samples are kept in EAMC_CLOCKS_DIR when it is set, else in the temp directory
+        base = os.environ.get("EAMC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = Path(base) / f"clocks_{os.getpid()}.csv"
 
     def __enter__(self):
         self.path.parent.mkdir(exist_ok=True)
@@ -369,6 +372,55 @@ def bench_uneven(S: int = 100, iters: int = 3):
             "ms": ms, "attempts_per_ns": attempts_per_sweep * S * iters / (ms * 1e6), "launch": best}
 
 
+def bench_recursion(L: int = 8, n: int = 256, iters: int = 24, S: int = 2000, P: int = 20000):
+    """Weight recursions side by side: the plain step and Berg's accumulated error-weighted one,
+    flat and power-law ensembles, n chains of L^3, `iters` iterations of S sweeps, then P
+    production sweeps with frozen weights.  Reported per variant: round trips in production
+    (the paper's figure of merit), chains without one, mean lowest energy, median spread
+    ln(max H / min H) of the production histogram between the lowest visited bin and E_top,
+    and the device time of one weight update over all chains."""
+    import numpy as np
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    out = {"workload": f"3D L={L}, {n} realizations (seed 3), {iters} x {S} iteration sweeps, "
+                       f"{P} production sweeps"}
+    stream = torch.cuda.Stream()
+    for kind, kname in ((eamc.EA_FLAT, "flat"), (eamc.EA_POWERLAW, "power_law")):
+        for mode, mname in ((eamc.EA_REC_PLAIN, "plain"), (eamc.EA_REC_BERG, "berg")):
+            ctx = eamc.Context(seed=3, device=0, stream=stream.cuda_stream)
+            ctx.init_disorder(3, L, n, rid0=0)
+            ctx.set_ensemble(0, n, kind, -3.6, 96.0)
+            ctx.set_recursion(0, n, mode)
+            upd_ms = []
+            for it in range(iters):
+                ctx.run_sweeps(S)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.update_weights()
+                e1.record(stream)
+                stream.synchronize()
+                upd_ms.append(e0.elapsed_time(e1))
+            ctx.set_eg(0, n, None)
+            ctx.roundtrips(reset=True)
+            ctx.histograms(reset=True)
+            ctx.run_sweeps(P, count_roundtrips=True)
+            H, R, D = ctx.histograms(), ctx.roundtrips(), ctx.describe()
+            spread = []
+            for k in range(n):
+                h = H[k, :D[k]["b_top"] + 1]
+                seg = h[np.nonzero(h)[0].min():].astype(float)
+                spread.append(float(np.log(seg.max() / max(seg.min(), 1.0))))
+            nrt = np.array([r["n_rt"] for r in R])
+            out[f"{kname}_{mname}"] = {
+                "round_trips": int(nrt.sum()), "chains_without_rt": int((nrt == 0).sum()),
+                "e_min_mean": float(np.mean([r["e_min"] for r in R])),
+                "spread_median": float(np.median(spread)),
+                "update_ms": float(np.median(upd_ms[1:]))}
+            ctx.close()
+    return out
+
+
 def bench_serving(window_s: float = 4.0, drain_s: float = 20.0):
     """Serving: Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12}, round-trip
     targets log-uniform in [10, 1000]; device-resident state, memory-based admission."""
@@ -421,7 +473,8 @@ def main():
         return
 
     if args.only:
-        fn = {"pt": lambda: bench_pt(args.pt_sweeps), "uneven": bench_uneven, "serving": bench_serving}
+        fn = {"pt": lambda: bench_pt(args.pt_sweeps), "uneven": bench_uneven, "serving": bench_serving,
+              "recursion": bench_recursion}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
     if world > 1:
@@ -433,7 +486,8 @@ def main():
     r = run_gpu(args, rank, world)
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = {"pt": bench_pt(), "uneven": bench_uneven(), "serving": bench_serving()}
+        extras = {"pt": bench_pt(), "uneven": bench_uneven(), "serving": bench_serving(),
+                  "recursion": bench_recursion()}
     if rank != 0:
         if world > 1:
             import torch

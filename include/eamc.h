@@ -58,6 +58,10 @@ extern "C" {
 #define EA_ONE_OVER_K 2 /* W ~ 1/k, k(E) = sum_{E_g<=E'<=E} Omega(E') (Eq. "1/k") */
 #define EA_CANON 3      /* W = exp(-beta E) (textbook Metropolis) */
 
+/* weight recursions (muca_set_recursion) */
+#define EA_REC_PLAIN 0  /* the plain step of muca_update_weights */
+#define EA_REC_BERG 1   /* Berg's accumulated error-weighted recursion */
+
 typedef struct ea_ctx ea_ctx;
 
 /* Round-trip record of one chain (Sec. III).  phase: 0 = waiting for the first visit of
@@ -148,7 +152,9 @@ int muca_set_sweep_multiplier(ea_ctx *ctx, int L, int multiplier);
 /* a8 -- captures n_iter iterations of [muca_run_sweeps(sweeps_per_iter, count_roundtrips),
  * then muca_update_weights if update_weights] into a CUDA graph on the context stream (which
  * must not be the legacy default stream).  ea_graph_launch replays it; ea_graph_release
- * frees it.  Replays see the launch configuration at capture time. */
+ * frees it.  Replays see the launch configuration at capture time.  Adding chains
+ * (ea_init_disorder), loading a snapshot and the first EA_REC_BERG recursion release the graph
+ * (the arenas it points into may move); ea_graph_launch then returns EA_ESTATE. */
 int ea_graph_capture(ea_ctx *ctx, int n_iter, uint64_t sweeps_per_iter, int count_roundtrips,
                      int update_weights);
 int ea_graph_launch(ea_ctx *ctx, int replays);
@@ -161,6 +167,26 @@ int ea_graph_release(ea_ctx *ctx);
  * thresholds are re-quantised.  Chains of kind EA_ONE_OVER_K / EA_CANON are untouched. */
 int muca_update_weights(ea_ctx *ctx);
 
+/* f1 -- chooses the weight recursion of chains chain0..chain0+n-1 (mode EA_REC_PLAIN or
+ * EA_REC_BERG) and empties their accumulators.  EA_REC_BERG is Berg's accumulated form
+ * (B. A. Berg, J. Stat. Phys. 82, 323 (1996); one of the iterative procedures collected in
+ * Janke 2003, which Sec. II refers to): for each pair of neighbouring bins (b, b+1) visited in
+ * an iteration, s = [ln H(b+1) - ln W(b+1)] - [ln H(b) - ln W(b)] estimates
+ * ln Omega(b+1) - ln Omega(b) with inverse Poisson variance g = H(b)H(b+1)/(H(b)+H(b+1)); the
+ * chain keeps D(b) (the g-weighted mean of all its estimates) and G(b) (the sum of the g), and
+ * muca_update_weights then sets ln W(b) - ln W(b+1) = ln P_SH(b) - ln P_SH(b+1) + D(b) where
+ * G(b) > 0 and the plain step's difference elsewhere, ln W(b_top) = 0.  An iteration run with
+ * weights that are constant over the range adds no estimates (every move inside the range is
+ * then accepted, so the sequential sweep is deterministic).  The first EA_REC_BERG call of a
+ * context allocates 16 bytes per bin of every chain and releases a captured graph.
+ * EA_EINVAL: bad range or mode; EA_ENOMEM: allocation failed. */
+int muca_set_recursion(ea_ctx *ctx, int chain0, int n, int mode);
+
+/* Berg accumulators of chains chain0..: out[c*stride + 2b] = D(b), out[c*stride + 2b + 1] = G(b)
+ * for b = 0..b_top(c) (host buffer; stride in doubles, >= 2 (b_top+1); the entry at b_top is
+ * unused and 0).  EA_ESTATE if no chain of the context ever used EA_REC_BERG. */
+int muca_get_recursion_state(ea_ctx *ctx, int chain0, int n, double *out, int stride);
+
 /* a5 -- rebuilds ln W of chains chain0..chain0+n-1 for a new ensemble from the density of
  * states implied by the current weights (ln Omega = ln P_SH(current kind) - ln W), see
  * EA_FLAT..EA_CANON, then re-quantises.  The new kind and parameters are recorded. */
@@ -170,7 +196,7 @@ int muca_build_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
 /* a9 -- serving support.  Re-initialises the listed chains (host int32 chain indices)
  * in place as new jobs: realization rids[k] with stream streams[k] (host uint32 arrays),
  * couplings and spins drawn from the seed, deterministic descent to E <= E_top, flat weights,
- * kind EA_FLAT, sweep counter 0, cleared histogram and round trips.  The chain keeps its L.
+ * kind EA_FLAT, recursion EA_REC_PLAIN, sweep counter 0, cleared histogram and round trips.  The chain keeps its L.
  * Other chains of the context are untouched, so their trajectories do not change. */
 int ea_reset_chains(ea_ctx *ctx, const int32_t *chains, int n, const uint32_t *rids,
                     const uint32_t *streams);
@@ -192,7 +218,8 @@ int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stride, int32_t
 /* Checkpoint / resume (not in the paper; random words are keyed by each chain's sweep
  * counter, so a run resumed from a snapshot continues the identical trajectory).  size gives
  * the snapshot's byte count; save writes the MUCA state of every chain (lattices, chain
- * states, weights, histograms, thresholds, launch layout, seed) into a host buffer of at least
+ * states, weights, histograms, thresholds, Berg accumulators, launch layout, seed) into a host
+ * buffer of at least
  * that size; load restores it into a context that has no chains yet (PT state and the launch
  * configuration are not part of a snapshot). */
 int ea_snapshot_size(ea_ctx *ctx, size_t *bytes);

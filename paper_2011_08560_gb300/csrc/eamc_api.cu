@@ -270,6 +270,13 @@ int eamc::ctx_refresh_chains(ea_ctx *ctx) {
 }
 
 // tile ids ordered by decreasing lattice volume (longest tiles first, for the work queue)
+void eamc::ctx_drop_graph(ea_ctx *ctx) {
+    if (ctx->graph_exec || ctx->graph) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    ctx->graph_sweeps = 0;
+}
+
 int eamc::ctx_rebuild_order(ea_ctx *ctx) {
     const size_t n = ctx->tiles.size();
     std::vector<int32_t> order(n);
@@ -326,7 +333,7 @@ extern "C" void ea_destroy(ea_ctx *ctx) {
     if (ctx->d_queue) cudaFree(ctx->d_queue);
     void *ptrs[] = {ctx->d_tiles, ctx->d_slots, ctx->d_spins,   ctx->d_bonds, ctx->d_lnW,
                     ctx->d_hist,  ctx->d_thr ? ctx->d_thr - kThrPad : nullptr,
-                    ctx->d_scratch, ctx->d_err, ctx->d_Jin};
+                    ctx->d_scratch, ctx->d_err, ctx->d_Jin, ctx->d_acc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -343,6 +350,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     if (stream >= (1u << 24)) return fail(EA_EINVAL, "stream must be < 2^24");
     if (ctx->dim && ctx->dim != dim) return fail(EA_EINVAL, "a context holds a single dim");
     EA_CUDA(cudaSetDevice(ctx->device));
+    ctx_drop_graph(ctx);  // the arenas may move and the tile set changes
     int smem_optin = 0;
     EA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (sweep_smem_bytes(dim, L) > (size_t)smem_optin)
@@ -381,6 +389,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
         (rc = grow(&ctx->d_hist, &ctx->hist_cap, ctx->w_used, w_used, ctx->stream)) ||
         (rc = grow_thr(ctx, w_used * 8)))
         return rc;
+    if (ctx->d_acc && (rc = grow(&ctx->d_acc, &ctx->acc_cap, ctx->w_used, w_used, ctx->stream))) return rc;
     EA_CUDA(cudaMemcpyAsync(ctx->d_tiles + tile0, nt.data(), new_tiles * sizeof(TileDesc),
                             cudaMemcpyHostToDevice, ctx->stream));
     // per-slot identity (rid, stream, defaults)
@@ -480,6 +489,35 @@ extern "C" int muca_set_ensemble(ea_ctx *ctx, int chain0, int n, int kind, doubl
     return EA_OK;
 }
 
+__global__ void set_recursion_kernel(SlotState *__restrict__ slots, const int32_t *__restrict__ slot_of,
+                                     const uint64_t *__restrict__ off, const int32_t *__restrict__ len, int n,
+                                     int mode, double2 *__restrict__ acc) {
+    const int c = blockIdx.x;
+    if (c >= n) return;
+    if (acc)
+        for (int b = threadIdx.x; b < len[c]; b += blockDim.x) acc[off[c] + b] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) slots[slot_of[c]].recursion = mode;
+}
+
+extern "C" int muca_set_recursion(ea_ctx *ctx, int chain0, int n, int mode) {
+    int rc = ctx_check_range(ctx, chain0, n);
+    if (rc) return rc;
+    if (mode != EA_REC_PLAIN && mode != EA_REC_BERG) return fail(EA_EINVAL, "unknown recursion %d", mode);
+    if (n == 0) return EA_OK;
+    if (mode == EA_REC_BERG && !ctx->d_acc) {
+        ctx_drop_graph(ctx);  // a captured update would not see the new accumulators
+        if ((rc = grow(&ctx->d_acc, &ctx->acc_cap, 0, ctx->w_used, ctx->stream))) return rc;
+    }
+    void *scr;
+    int32_t *d_slot, *d_len;
+    uint64_t *d_off;
+    if ((rc = ctx_range_meta(ctx, chain0, n, 0, &scr, &d_slot, &d_off, &d_len))) return rc;
+    set_recursion_kernel<<<n, 128, 0, ctx->stream>>>(ctx->d_slots, d_slot, d_off, d_len, n, mode, ctx->d_acc);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
 static int max_len(ea_ctx *ctx, int chain0, int n) {
     int m = 0;
     for (int k = 0; k < n; ++k) m = std::max(m, ctx->chain_btop[chain0 + k] + 1);
@@ -527,6 +565,11 @@ extern "C" int muca_set_weights(ea_ctx *ctx, int chain0, int n, const double *ln
 
 extern "C" int muca_get_weights(ea_ctx *ctx, int chain0, int n, double *lnW, int stride) {
     return table_io<double>(ctx, chain0, n, ctx ? ctx->d_lnW : nullptr, 1, lnW, stride, false);
+}
+
+extern "C" int muca_get_recursion_state(ea_ctx *ctx, int chain0, int n, double *out, int stride) {
+    if (ctx && !ctx->d_acc) return fail(EA_ESTATE, "no chain of this context uses the Berg recursion");
+    return table_io<double>(ctx, chain0, n, ctx ? (double *)ctx->d_acc : nullptr, 2, out, stride, false);
 }
 
 extern "C" int muca_set_thresholds(ea_ctx *ctx, int chain0, int n, const uint32_t *thr, int stride) {
@@ -655,7 +698,7 @@ extern "C" int ea_graph_capture(ea_ctx *ctx, int n_iter, uint64_t sweeps_per_ite
     for (int it = 0; it < n_iter && rc == EA_OK; ++it) {
         rc = enqueue_sweeps(ctx, sweeps_per_iter, count_roundtrips);
         if (rc == EA_OK && update_weights) {
-            cudaError_t e = launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->stream);
+            cudaError_t e = launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->d_acc, ctx->stream);
             if (e == cudaSuccess) e = launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream);
             if (e != cudaSuccess) rc = cuda_fail(e, "update in capture");
         }
@@ -697,7 +740,7 @@ extern "C" int muca_update_weights(ea_ctx *ctx) {
     if (!ctx) return fail(EA_EINVAL, "null context");
     if (ctx->tiles.empty()) return fail(EA_ESTATE, "no chains");
     const int nt = (int)ctx->tiles.size();
-    EA_CUDA(launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->stream));
+    EA_CUDA(launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->d_acc, ctx->stream));
     EA_CUDA(launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream));
     return EA_OK;
 }
@@ -782,7 +825,7 @@ extern "C" int muca_update_weights_subset(ea_ctx *ctx, const int32_t *chains, in
     int32_t *d_slot;
     int rc = upload_slots(ctx, chains, n, 0, &scr, &d_slot);
     if (rc) return rc;
-    EA_CUDA(launch_update_weights_sel(ctx->d_tiles, ctx->d_slots, ctx->d_lnW, ctx->d_hist, d_slot, n, ctx->stream));
+    EA_CUDA(launch_update_weights_sel(ctx->d_tiles, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->d_acc, d_slot, n, ctx->stream));
     EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW, ctx->d_thr,
                             ctx->stream));
     EA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -862,13 +905,13 @@ extern "C" int ea_synchronize(ea_ctx *ctx) {
 // ------------------------------------------------------------------------------ snapshots
 namespace {
 constexpr uint64_t kSnapMagic = 0x45414d43534e4150ull;  // "EAMCSNAP"
-constexpr uint32_t kSnapVersion = 1;
+constexpr uint32_t kSnapVersion = 2;
 
 struct SnapHeader {
     uint64_t magic;
     uint32_t version, dim;
     uint64_t seed, n_tiles, n_chains, spin_used, bond_used, w_used, max_t_host;
-    int32_t max_V, pad;
+    int32_t max_V, has_acc;  // has_acc: the Berg accumulators follow the thresholds
     uint64_t sweep_smem;
 };
 
@@ -883,7 +926,8 @@ static size_t snapshot_bytes(const ea_ctx *ctx) {
     const size_t nt = ctx->tiles.size(), nc = ctx->chain_slot.size();
     return sizeof(SnapHeader) + nt * sizeof(TileDesc) + nc * (sizeof(int32_t) * 2 + sizeof(uint64_t)) +
            nt * kTile * sizeof(SlotState) + (ctx->spin_used + ctx->bond_used) * sizeof(uint32_t) +
-           ctx->w_used * (sizeof(double) + sizeof(uint32_t) + 8 * sizeof(uint32_t));
+           ctx->w_used * (sizeof(double) + sizeof(uint32_t) + 8 * sizeof(uint32_t)) +
+           (ctx->d_acc ? ctx->w_used * sizeof(double2) : 0);
 }
 
 extern "C" int ea_snapshot_size(ea_ctx *ctx, size_t *bytes) {
@@ -911,6 +955,7 @@ extern "C" int ea_snapshot_save(ea_ctx *ctx, void *buf, size_t cap) {
     h.w_used = ctx->w_used;
     h.max_t_host = ctx->max_t_host;
     h.max_V = ctx->max_V;
+    h.has_acc = ctx->d_acc ? 1 : 0;
     h.sweep_smem = ctx->sweep_smem;
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -927,7 +972,7 @@ extern "C" int ea_snapshot_save(ea_ctx *ctx, void *buf, size_t cap) {
     if ((rc = dev(ctx->d_slots, h.n_tiles * kTile * sizeof(SlotState))) ||
         (rc = dev(ctx->d_spins, h.spin_used * 4)) || (rc = dev(ctx->d_bonds, h.bond_used * 4)) ||
         (rc = dev(ctx->d_lnW, h.w_used * 8)) || (rc = dev(ctx->d_hist, h.w_used * 4)) ||
-        (rc = dev(ctx->d_thr, h.w_used * 8 * 4)))
+        (rc = dev(ctx->d_thr, h.w_used * 8 * 4)) || (h.has_acc && (rc = dev(ctx->d_acc, h.w_used * 16))))
         return rc;
     return EA_OK;
 }
@@ -935,6 +980,7 @@ extern "C" int ea_snapshot_save(ea_ctx *ctx, void *buf, size_t cap) {
 extern "C" int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size) {
     if (!ctx || !buf) return fail(EA_EINVAL, "null argument");
     if (!ctx->tiles.empty()) return fail(EA_ESTATE, "a snapshot loads into a context without chains");
+    ctx_drop_graph(ctx);
     if (size < sizeof(SnapHeader)) return fail(EA_EINVAL, "snapshot too short");
     SnapHeader h;
     std::memcpy(&h, buf, sizeof h);
@@ -944,7 +990,7 @@ extern "C" int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size) {
     std::vector<int32_t> cslot(h.n_chains), cbtop(h.n_chains);
     std::vector<uint64_t> cwoff(h.n_chains);
     const size_t need = sizeof h + h.n_tiles * sizeof(TileDesc) + h.n_chains * 16 + h.n_tiles * kTile * sizeof(SlotState) +
-                        (h.spin_used + h.bond_used) * 4 + h.w_used * (8 + 4 + 32);
+                        (h.spin_used + h.bond_used) * 4 + h.w_used * (8 + 4 + 32) + (h.has_acc ? h.w_used * 16 : 0);
     if (size < need) return fail(EA_EINVAL, "snapshot truncated (%zu of %zu bytes)", size, need);
     std::memcpy(tiles.data(), p, h.n_tiles * sizeof(TileDesc)); p += h.n_tiles * sizeof(TileDesc);
     std::memcpy(cslot.data(), p, h.n_chains * 4); p += h.n_chains * 4;
@@ -957,7 +1003,8 @@ extern "C" int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size) {
         (rc = grow(&ctx->d_bonds, &ctx->bonds_cap, 0, h.bond_used, ctx->stream)) ||
         (rc = grow(&ctx->d_lnW, &ctx->lnW_cap, 0, h.w_used, ctx->stream)) ||
         (rc = grow(&ctx->d_hist, &ctx->hist_cap, 0, h.w_used, ctx->stream)) ||
-        (rc = grow_thr(ctx, h.w_used * 8)))
+        (rc = grow_thr(ctx, h.w_used * 8)) ||
+        (h.has_acc && (rc = grow(&ctx->d_acc, &ctx->acc_cap, 0, h.w_used, ctx->stream))))
         return rc;
     EA_CUDA(cudaStreamSynchronize(ctx->stream));
     auto dev = [&](void *dst, size_t bytes) -> int {
@@ -968,7 +1015,8 @@ extern "C" int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size) {
     EA_CUDA(cudaMemcpy(ctx->d_tiles, tiles.data(), h.n_tiles * sizeof(TileDesc), cudaMemcpyHostToDevice));
     if ((rc = dev(ctx->d_slots, h.n_tiles * kTile * sizeof(SlotState))) || (rc = dev(ctx->d_spins, h.spin_used * 4)) ||
         (rc = dev(ctx->d_bonds, h.bond_used * 4)) || (rc = dev(ctx->d_lnW, h.w_used * 8)) ||
-        (rc = dev(ctx->d_hist, h.w_used * 4)) || (rc = dev(ctx->d_thr, h.w_used * 8 * 4)))
+        (rc = dev(ctx->d_hist, h.w_used * 4)) || (rc = dev(ctx->d_thr, h.w_used * 8 * 4)) ||
+        (h.has_acc && (rc = dev(ctx->d_acc, h.w_used * 16))))
         return rc;
     ctx->dim = (int)h.dim;
     ctx->seed = h.seed;

@@ -33,6 +33,8 @@ struct ea_ctx {
     size_t tiles_cap = 0, slots_cap = 0, spins_cap = 0, bonds_cap = 0, lnW_cap = 0, hist_cap = 0,
            thr_cap = 0;
     size_t spin_used = 0, bond_used = 0, w_used = 0;
+    double2 *d_acc = nullptr;         // f1: Berg accumulators {D, G} per bin (allocated on first use)
+    size_t acc_cap = 0;
 
     // staging / scratch for marshalling (grown on demand)
     void *d_scratch = nullptr;
@@ -64,6 +66,7 @@ int ctx_range_meta(ea_ctx *ctx, int chain0, int n, size_t extra, void **scratch,
                    uint64_t **d_off, int32_t **d_len);
 int ctx_refresh_chains(ea_ctx *ctx);
 int ctx_rebuild_order(ea_ctx *ctx);
+void ctx_drop_graph(ea_ctx *ctx);
 }  // namespace eamc
 
 void pt_release(ea_ctx *ctx);

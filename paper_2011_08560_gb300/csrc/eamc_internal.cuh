@@ -36,7 +36,7 @@ struct SlotState {
     uint64_t t;                       // sweeps done
     uint32_t rid, stream;
     int32_t kind, active;
-    int32_t requeue, pad0;
+    int32_t requeue, recursion;       // recursion: 0 plain weight step, 1 Berg's accumulated one
     double alpha, pole, beta;         // ensemble parameters
 };
 
@@ -71,7 +71,7 @@ cudaError_t launch_quantize(const TileDesc *d_tiles, int n_tiles, const SlotStat
 cudaError_t launch_enforce_walls(const TileDesc *d_tiles, int n_tiles, const SlotState *d_slots,
                                  uint32_t *d_thr, cudaStream_t st);
 cudaError_t launch_update_weights(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
-                                  double *d_lnW, uint32_t *d_hist, cudaStream_t st);
+                                  double *d_lnW, uint32_t *d_hist, double2 *d_acc, cudaStream_t st);
 cudaError_t launch_build_ensemble(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
                                   const uint8_t *d_sel, int kind, double alpha, double pole,
                                   double beta, double *d_lnW, cudaStream_t st);
@@ -80,7 +80,8 @@ cudaError_t launch_reset_lanes(const TileDesc *d_tiles, int dim, SlotState *d_sl
                                const uint32_t *d_rids, const uint32_t *d_streams, int n, PhiloxKey key,
                                int *d_err, cudaStream_t st);
 cudaError_t launch_update_weights_sel(const TileDesc *d_tiles, SlotState *d_slots, double *d_lnW,
-                                      uint32_t *d_hist, const int32_t *d_slot_of, int n, cudaStream_t st);
+                                      uint32_t *d_hist, double2 *d_acc, const int32_t *d_slot_of, int n,
+                                      cudaStream_t st);
 cudaError_t launch_reset_rt(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
                             const uint8_t *d_sel, cudaStream_t st);
 

@@ -155,22 +155,76 @@ __device__ __forceinline__ double ln_profile(int kind, double alpha, double pole
 
 // one block per chain; threads over bins
 __device__ void update_weights_one(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
-                                   double *__restrict__ lnW, uint32_t *__restrict__ hist, int slot);
+                                   double *__restrict__ lnW, uint32_t *__restrict__ hist,
+                                   double2 *__restrict__ acc, int slot);
 
 __global__ void update_weights_kernel(const TileDesc *__restrict__ tiles,
                                       SlotState *__restrict__ slots, double *__restrict__ lnW,
-                                      uint32_t *__restrict__ hist) {
-    update_weights_one(tiles, slots, lnW, hist, blockIdx.x);
+                                      uint32_t *__restrict__ hist, double2 *__restrict__ acc) {
+    update_weights_one(tiles, slots, lnW, hist, acc, blockIdx.x);
 }
 
 __global__ void update_weights_sel_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
                                           double *__restrict__ lnW, uint32_t *__restrict__ hist,
-                                          const int32_t *__restrict__ slot_of) {
-    update_weights_one(tiles, slots, lnW, hist, slot_of[blockIdx.x]);
+                                          double2 *__restrict__ acc, const int32_t *__restrict__ slot_of) {
+    update_weights_one(tiles, slots, lnW, hist, acc, slot_of[blockIdx.x]);
+}
+
+// Largest table row count: 3D, L = 12 -> (3 * 1728 / 2 >> 1) + 1 bins.
+constexpr int kMaxRows = 1297;
+
+// Berg's accumulated error-weighted recursion (B. A. Berg, J. Stat. Phys. 82, 323 (1996), one of
+// the iterative procedures Sec. II refers to).  Per pair of neighbouring bins (b, b+1) that were
+// both visited this iteration, s = [ln H(b+1) - ln W(b+1)] - [ln H(b) - ln W(b)] estimates
+// ln Omega(b+1) - ln Omega(b) with inverse variance g = H(b) H(b+1) / (H(b) + H(b+1));
+// acc[b] = {D, G} holds the g-weighted mean of all estimates and the sum of the g.  New weights:
+// ln W(b) - ln W(b+1) = ln P_SH(b) - ln P_SH(b+1) + D(b) where G(b) > 0, the plain step's
+// difference elsewhere, ln W(b_top) = 0.  Weights constant over the range add no estimates (the
+// sweep is then deterministic, every move inside the range being accepted).
+__device__ void update_weights_berg(const TileDesc &td, const SlotState &ss, double *__restrict__ w,
+                                    const uint32_t *__restrict__ h, double2 *__restrict__ acc, int e_g) {
+    __shared__ double diff[kMaxRows];
+    const int nb = td.dim * td.V, bt = ss.b_top;
+    int changed = 0;
+    for (int b = threadIdx.x; b < bt; b += blockDim.x) changed |= (w[b] != w[bt]);
+    const bool informative = __syncthreads_or(changed) != 0;
+    for (int b = threadIdx.x; b < bt; b += blockDim.x) {
+        const double lp0 = ln_profile(ss.kind, ss.alpha, ss.pole, e_g, energy_of_bin(nb, ss.parity, b));
+        const double lp1 = ln_profile(ss.kind, ss.alpha, ss.pole, e_g, energy_of_bin(nb, ss.parity, b + 1));
+        const uint32_t c0 = h[b], c1 = h[b + 1];
+        double2 a = acc[b];
+        if (informative && c0 > 0u && c1 > 0u) {
+            const double h0 = (double)c0, h1 = (double)c1;
+            const double s = __dsub_rn(__dsub_rn(log(h1), w[b + 1]), __dsub_rn(log(h0), w[b]));
+            const double g = __ddiv_rn(__dmul_rn(h0, h1), __dadd_rn(h0, h1));
+            a.x = __ddiv_rn(__dadd_rn(__dmul_rn(a.y, a.x), __dmul_rn(g, s)), __dadd_rn(a.y, g));
+            a.y = __dadd_rn(a.y, g);
+            acc[b] = a;
+        }
+        if (a.y > 0.0) {
+            diff[b] = __dadd_rn(__dsub_rn(lp0, lp1), a.x);
+        } else {
+            const double a0 = w[b] + lp0 - log(c0 > 0u ? (double)c0 : 1.0);
+            const double a1 = w[b + 1] + lp1 - log(c1 > 0u ? (double)c1 : 1.0);
+            diff[b] = a0 - a1;
+        }
+    }
+    __syncthreads();
+    // every thread has read the old w it needs; the suffix sum runs in the order of the
+    // definition (top bin down), O(bins) on one thread per chain
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        w[bt] = 0.0;
+        for (int b = bt - 1; b >= 0; --b) {
+            v = __dadd_rn(v, diff[b]);
+            w[b] = v;
+        }
+    }
 }
 
 __device__ void update_weights_one(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
-                                   double *__restrict__ lnW, uint32_t *__restrict__ hist, int slot) {
+                                   double *__restrict__ lnW, uint32_t *__restrict__ hist,
+                                   double2 *__restrict__ acc, int slot) {
     const TileDesc td = tiles[slot / kTile];
     const int lane = slot % kTile;
     SlotState ss = slots[slot];
@@ -179,6 +233,17 @@ __device__ void update_weights_one(const TileDesc *__restrict__ tiles, SlotState
     const int e_g = energy_of_bin(nb, ss.parity, ss.b_min);
     double *w = lnW + td.w_base + (uint64_t)lane * td.B;
     uint32_t *h = hist + td.w_base + (uint64_t)lane * td.B;
+    if (ss.recursion == 1 && acc) {
+        update_weights_berg(td, ss, w, h, acc + td.w_base + (uint64_t)lane * td.B, e_g);
+        __syncthreads();
+        for (int b = threadIdx.x; b <= ss.b_top; b += blockDim.x) h[b] = 0u;
+        if (threadIdx.x == 0) {
+            ss.e_g = e_g;
+            ss.b_g = ss.b_min;
+            slots[slot] = ss;
+        }
+        return;
+    }
     auto next = [&](int b) {
         const int E = energy_of_bin(nb, ss.parity, b);
         const double hb = h[b] > 0u ? (double)h[b] : 1.0;
@@ -385,6 +450,7 @@ __global__ void reset_lane_kernel(const TileDesc *__restrict__ tiles, SlotState 
     ss.t = 0;
     ss.requeue = 0;
     ss.kind = 0;
+    ss.recursion = 0;
     ss.active = stuck ? 0 : 1;
     slots[slot] = ss;
     if (stuck) atomicExch(err, 1);
@@ -392,9 +458,6 @@ __global__ void reset_lane_kernel(const TileDesc *__restrict__ tiles, SlotState 
 
 // weight update of selected chains only (serving: jobs reach iteration boundaries at
 // different times)
-__global__ void update_weights_sel_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
-                                          double *__restrict__ lnW, uint32_t *__restrict__ hist,
-                                          const int32_t *__restrict__ slot_of);
 
 __global__ void reset_rt_kernel(const TileDesc *__restrict__ tiles, int n_slots,
                                 SlotState *__restrict__ slots, const uint8_t *__restrict__ sel) {
@@ -442,9 +505,9 @@ cudaError_t launch_enforce_walls(const TileDesc *d_tiles, int n_tiles, const Slo
 }
 
 cudaError_t launch_update_weights(const TileDesc *d_tiles, int n_tiles, SlotState *d_slots,
-                                  double *d_lnW, uint32_t *d_hist, cudaStream_t st) {
+                                  double *d_lnW, uint32_t *d_hist, double2 *d_acc, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    update_weights_kernel<<<n_tiles * kTile, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_hist);
+    update_weights_kernel<<<n_tiles * kTile, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_hist, d_acc);
     return cudaGetLastError();
 }
 
@@ -473,9 +536,10 @@ cudaError_t launch_reset_lanes(const TileDesc *d_tiles, int dim, SlotState *d_sl
 }
 
 cudaError_t launch_update_weights_sel(const TileDesc *d_tiles, SlotState *d_slots, double *d_lnW,
-                                      uint32_t *d_hist, const int32_t *d_slot_of, int n, cudaStream_t st) {
+                                      uint32_t *d_hist, double2 *d_acc, const int32_t *d_slot_of, int n,
+                                      cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    update_weights_sel_kernel<<<n, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_hist, d_slot_of);
+    update_weights_sel_kernel<<<n, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_hist, d_acc, d_slot_of);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ from .build import LIB
 EA_OK, EA_EINVAL, EA_ENOMEM, EA_ECUDA, EA_ETIMEOUT, EA_ESTATE = 0, -1, -2, -3, -4, -5
 EA_ALWAYS = 0xFFFFFFFF
 EA_FLAT, EA_POWERLAW, EA_ONE_OVER_K, EA_CANON = 0, 1, 2, 3
+EA_REC_PLAIN, EA_REC_BERG = 0, 1
 
 
 class EamcError(RuntimeError):
@@ -64,6 +65,8 @@ SIGNATURES = {
     "muca_set_eg": (_i, [P, _i, _i, P]),
     "muca_run_sweeps": (_i, [P, _u64, _i]),
     "muca_update_weights": (_i, [P]),
+    "muca_set_recursion": (_i, [P, _i, _i, _i]),
+    "muca_get_recursion_state": (_i, [P, _i, _i, P, _i]),
     "muca_build_ensemble": (_i, [P, _i, _i, _i, _f64, _f64, _f64]),
     "get_histograms": (_i, [P, _i, _i, P, _i, _i]),
     "get_roundtrips": (_i, [P, _i, _i, P, _i]),
@@ -211,6 +214,18 @@ class Context:
     # a4
     def update_weights(self):
         check(lib().muca_update_weights(self._h))
+
+    # f1
+    def set_recursion(self, chain0: int, n: int, mode: int):
+        check(lib().muca_set_recursion(self._h, chain0, n, mode))
+
+    def recursion_state(self, chain0: int = 0, n: int | None = None, rows: int | None = None):
+        """Berg accumulators as float64 [n, rows, 2] = (D, G) per bin."""
+        n = self.num_chains() - chain0 if n is None else n
+        rows = self._rows(chain0, n) if rows is None else rows
+        out = np.zeros((n, rows, 2), dtype=np.float64)
+        check(lib().muca_get_recursion_state(self._h, chain0, n, _p(out), 2 * rows))
+        return out
 
     def histograms(self, chain0: int = 0, n: int | None = None, reset: bool = False,
                    rows: int | None = None):

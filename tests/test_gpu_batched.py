@@ -82,6 +82,8 @@ def test_graph_replay_matches_direct_calls(eamc):
     st = torch.cuda.Stream()
     ref = _mixed(eamc, st.cuda_stream)
     ctx = _mixed(eamc, st.cuda_stream)
+    for c in (ref, ctx):
+        c.set_recursion(30, 20, eamc.EA_REC_BERG)
     ctx.set_launch(True, 0)
     ctx.graph_capture(n_iter=2, sweeps_per_iter=25, count_roundtrips=True, update_weights=True)
     ctx.graph_launch(3)
@@ -89,7 +91,13 @@ def test_graph_replay_matches_direct_calls(eamc):
     _run(ref, 6, 25)
     ref.synchronize()
     _same(_state(ref), _state(ctx))
+    assert np.array_equal(ref.recursion_state(), ctx.recursion_state())
     ctx.graph_release()
+    with pytest.raises(eamc.EamcError):
+        ctx.graph_launch(1)
+    # adding chains may move the arenas: the captured graph is released
+    ctx.graph_capture(n_iter=1, sweeps_per_iter=5)
+    ctx.init_disorder(3, 4, 3, rid0=900)
     with pytest.raises(eamc.EamcError):
         ctx.graph_launch(1)
 
@@ -97,15 +105,18 @@ def test_graph_replay_matches_direct_calls(eamc):
 def test_snapshot_resume_is_bit_exact(eamc):
     """Run 2S sweeps straight vs S, snapshot, restore into a new context, S more."""
     straight = _mixed(eamc)
-    _run(straight, 2, 30)
+    straight.set_recursion(0, 40, eamc.EA_REC_BERG)
+    _run(straight, 4, 30)
     first = _mixed(eamc)
-    _run(first, 1, 30)
+    first.set_recursion(0, 40, eamc.EA_REC_BERG)
+    _run(first, 2, 30)
     blob = first.snapshot()
     resumed = eamc.Context(seed=999)          # the seed comes from the snapshot
     resumed.restore(blob)
     assert resumed.num_chains() == first.num_chains()
-    _run(resumed, 1, 30)
+    _run(resumed, 2, 30)
     _same(_state(straight), _state(resumed))
+    assert np.array_equal(straight.recursion_state(), resumed.recursion_state())
     with pytest.raises(eamc.EamcError):
         resumed.restore(blob)                 # only into a context without chains
     with pytest.raises(eamc.EamcError):

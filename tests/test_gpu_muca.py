@@ -185,6 +185,76 @@ def test_weight_iteration_parity(eamc, orc, kind):
         _compare_state(ctx, chains, hist=True, rt=False)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_berg_recursion_parity(eamc, orc, kind):
+    """Berg's accumulated recursion on every other chain, the plain step on the rest."""
+    dim, L, n = 3, 4, 37
+    alpha, pole = -3.6, 96.0
+    ctx = eamc.Context(seed=SEED)
+    ctx.init_disorder(dim, L, n, rid0=500)
+    ctx.set_ensemble(0, n, kind, alpha, pole)
+    berg = [k % 2 == 0 for k in range(n)]
+    for k in range(n):
+        if berg[k]:
+            ctx.set_recursion(k, 1, eamc.EA_REC_BERG)
+    chains = _oracle_chains(orc, dim, L, n, rid0=500)
+    lnW = [np.zeros(c.b_top + 1) for c in chains]
+    acc = [orc.berg_state(c.b_top + 1) for c in chains]
+    for it in range(6):
+        ctx.run_sweeps(150)
+        ctx.update_weights()
+        for k, c in enumerate(chains):
+            c.sweeps(150, orc.quantize(dim, lnW[k]))
+            if berg[k]:
+                lnW[k] = orc.update_weights_berg(dim, L, c.parity, kind, alpha, pole, c.rt.e_min,
+                                                 lnW[k], c.hist, acc[k])
+            else:
+                lnW[k] = orc.update_weights(dim, L, c.parity, kind, alpha, pole, c.rt.e_min,
+                                            lnW[k], c.hist)
+            c.hist[:] = 0
+        G = ctx.get_weights()
+        T = ctx.get_thresholds()
+        A = ctx.recursion_state()
+        for k, c in enumerate(chains):
+            assert _close(G[k, :c.b_top + 1], lnW[k]), (it, k)
+            _thresholds_agree(orc, dim, T[k], lnW[k])
+            want = acc[k] if berg[k] else np.zeros_like(acc[k])
+            assert _close(A[k, :c.b_top + 1, 0], want[0]), (it, k, "D")
+            assert _close(A[k, :c.b_top + 1, 1], want[1]), (it, k, "G")
+        _compare_state(ctx, chains, hist=True, rt=False)
+    assert np.any(A[0, :, 1] > 0)
+
+
+def test_berg_subset_update_and_reset(eamc, orc):
+    dim, L, n = 3, 5, 6
+    ctx = eamc.Context(seed=SEED)
+    ctx.init_disorder(dim, L, n, rid0=600)
+    ctx.set_recursion(0, n, eamc.EA_REC_BERG)
+    chains = _oracle_chains(orc, dim, L, n, rid0=600)
+    lnW = [np.zeros(c.b_top + 1) for c in chains]
+    acc = [orc.berg_state(c.b_top + 1) for c in chains]
+    sel = [1, 4]
+    for it in range(3):
+        ctx.run_sweeps(80)
+        for c, w in zip(chains, lnW):
+            c.sweeps(80, orc.quantize(dim, w))
+        ctx.update_weights_subset(sel)
+        for k in sel:
+            c = chains[k]
+            lnW[k] = orc.update_weights_berg(dim, L, c.parity, 0, -3.6, 96.0, c.rt.e_min, lnW[k],
+                                             c.hist, acc[k])
+            c.hist[:] = 0
+    G = ctx.get_weights()
+    for k, c in enumerate(chains):
+        assert _close(G[k, :c.b_top + 1], lnW[k]), k
+    # re-setting the recursion empties the accumulators; a lane reset returns it to plain
+    ctx.set_recursion(1, 1, eamc.EA_REC_BERG)
+    assert not ctx.recursion_state(1, 1).any()
+    assert ctx.recursion_state(4, 1)[0, :, 1].any()
+    with pytest.raises(eamc.EamcError):
+        ctx.set_recursion(0, 1, 7)
+
+
 @pytest.mark.parametrize("kind", [0, 1, 2, 3])
 def test_build_ensemble_parity(eamc, orc, kind):
     dim, L, n = 3, 4, 6
