@@ -15,6 +15,8 @@ What each function follows (Mueller, Schnabel, Janke, arXiv:2011.08560):
   update_weights_berg ........ Sec. II / Janke 2003: Berg's accumulated error-weighted recursion
   build_weights .............. Eq. "muca-weights", nonflat weight, Eq. "1/k", canonical
   pt_tables / pt_sweeps ...... Sec. II, parallel tempering and Eq. "temperatureexchange"
+  pt_colour .................. sweep order of PT (checkerboard for even L, 3 colours for odd L)
+  pt_adapt ................... Sec. II, PT: constant exchange rates by moving the temperatures
   round trips ................ Sec. III (top -> E_g -> top, times in sweeps)
   dos_bruteforce ............. exact g(E) by enumeration (used to pin the chain)
 
@@ -91,6 +93,9 @@ def lib():
             "or_update_weights_berg": (None, [i32, i32, i32, i32, i32, f64, f64, i32, P, P, P, P]),
             "or_build_weights": (None, [i32, i32, i32, i32, i32, f64, f64, f64, i32, P, P]),
             "or_pt_tables": (None, [i32, i32, P, i32, P, P]),
+            "or_pt_colours": (i32, [i32]),
+            "or_pt_colour": (i32, [i32, i32, i32]),
+            "or_pt_adapt": (None, [i32, P, P, P, f64]),
             "or_pt_sweeps": (i32, [i32, i32, u64, u32, i32, P, P, P, P, u64, u64, P, P, i32,
                                    P, i32, i32, i32, P]),
             "or_dos_bruteforce": (i32, [i32, i32, P, P]),
@@ -261,6 +266,33 @@ def pt_tables(dim: int, betas, dmax: int):
     return thr_k, thr_pair
 
 
+def pt_colour(dim: int, L: int, i: int) -> int:
+    return lib().or_pt_colour(dim, L, i)
+
+
+def pt_colours(L: int) -> int:
+    return lib().or_pt_colours(L)
+
+
+def pt_attempts(M: int, t0: int, t1: int) -> np.ndarray:
+    """Exchange attempts of each pair (k, k+1) in sweeps t0..t1-1 (pair k is tried when
+    t = k mod 2)."""
+    n = t1 - t0
+    out = np.zeros(max(M - 1, 1), dtype=np.uint64)
+    for k in range(M - 1):
+        first = t0 + ((k - t0) % 2)          # first t >= t0 with t = k (mod 2)
+        out[k] = 0 if first >= t1 else (t1 - 1 - first) // 2 + 1
+    return out
+
+
+def pt_adapt(betas, n_acc, n_att, eta: float) -> np.ndarray:
+    b = np.ascontiguousarray(betas, dtype=np.float64).copy()
+    acc = np.ascontiguousarray(n_acc, dtype=np.uint64)
+    att = np.ascontiguousarray(n_att, dtype=np.uint64)
+    lib().or_pt_adapt(b.shape[0], _p(b), _p(acc), _p(att), eta)
+    return b
+
+
 class PTRealization:
     """M replicas of one realization under parallel tempering, advanced by the oracle."""
 
@@ -284,6 +316,20 @@ class PTRealization:
             self.rt[k].t_last = -1
             self.rt[k].e_min = int(self.E[k])
         self.swap_acc = np.zeros(max(self.M - 1, 1), dtype=np.uint64)
+        self._win_t, self._win_acc = 0, self.swap_acc.copy()
+
+    def set_betas(self, betas):
+        self.betas = np.ascontiguousarray(betas, dtype=np.float64)
+        self.thr_k, self.thr_pair = pt_tables(self.dim, self.betas, self.dmax)
+
+    def window_rates(self):
+        """(accepted, attempted) exchanges per pair since the last adapt()."""
+        return self.swap_acc - self._win_acc, pt_attempts(self.M, self._win_t, self.t)
+
+    def adapt(self, eta: float):
+        acc, att = self.window_rates()
+        self.set_betas(pt_adapt(self.betas, acc, att, eta))
+        self._win_t, self._win_acc = self.t, self.swap_acc.copy()
 
     def sweeps(self, n: int, count_rt: bool = False, e_g: int = 0, e_hot: int = 0):
         rc = lib().or_pt_sweeps(self.dim, self.L, self.seed, self.rid, self.M, _p(self.J),
@@ -291,5 +337,5 @@ class PTRealization:
                                 _p(self.thr_k), _p(self.thr_pair), self.dmax, self.rt,
                                 int(count_rt), e_g, e_hot, _p(self.swap_acc))
         if rc != 0:
-            raise ValueError("PT needs an even L (checkerboard)")
+            raise ValueError("or_pt_sweeps failed")
         self.t += n

@@ -395,27 +395,47 @@ static uint32_t pt_rand(uint64_t seed, uint32_t rid, int slot, int i, uint64_t t
     return r;
 }
 
+/* Colour of a coordinate along one axis for odd L: x mod 3, except that the last position
+ * takes colour 1 when x mod 3 would give it colour 0 (L = 1 mod 3), the colour of its
+ * periodic neighbour x = 0.  Neighbouring positions (periodically) never share a colour. */
+static int odd_axis_colour(int L, int x) {
+    if (x == L - 1 && (L - 1) % 3 == 0) return 1;
+    return x % 3;
+}
+
+/* Colour classes of the PT sweep.  Even L: the checkerboard, colour (x + y + z) mod 2.
+ * Odd L (the checkerboard is not a proper colouring under periodic boundaries): colour
+ * (c(x) + c(y) + c(z)) mod 3 with c from odd_axis_colour; a step to a neighbour changes one
+ * of c(x), c(y), c(z) by 1 or 2 (mod 3), so neighbours always differ in colour. */
+int or_pt_colours(int L) { return (L % 2 == 0) ? 2 : 3; }
+
+int or_pt_colour(int dim, int L, int i) {
+    int x = i % L, y = (i / L) % L, zz = (dim == 3) ? i / (L * L) : 0;
+    if (L % 2 == 0) return (x + y + zz) & 1;
+    int c = odd_axis_colour(L, x) + odd_axis_colour(L, y) + (dim == 3 ? odd_axis_colour(L, zz) : 0);
+    return c % 3;
+}
+
 /* One realization, M replicas.  S holds the configuration currently at slot k in
  * S[k*V ...]; E[k] its energy; label[k] the replica (configuration) number at slot k.
- * Per sweep t: every slot gets a checkerboard Metropolis sweep (sites with even
- * coordinate sum first, each colour in lexicographic order); then exchanges between
- * slots (k, k+1) for k = t mod 2, t mod 2 + 2, ...; then, if count_rt, one round-trip
- * check per replica with bottom e_g and top e_hot (Sec. III). rt is indexed by label. */
+ * Per sweep t: every slot gets a Metropolis sweep colour class by colour class (or_pt_colour;
+ * each class in lexicographic order); then exchanges between slots (k, k+1) for
+ * k = t mod 2, t mod 2 + 2, ...; then, if count_rt, one round-trip check per replica with
+ * bottom e_g and top e_hot (Sec. III). rt is indexed by label. */
 int or_pt_sweeps(int dim, int L, uint64_t seed, uint32_t rid, int M, const int8_t *J,
                  int8_t *S, int32_t *E, int32_t *label, uint64_t t0, uint64_t n_sweeps,
                  const uint32_t *thr_k, const uint32_t *thr_pair, int dmax, or_rt *rt,
                  int count_rt, int e_g, int e_hot, uint64_t *swap_acc) {
     int V = or_volume(dim, L), z = 2 * dim;
-    if (L % 2) return -1;
+    int ncol = or_pt_colours(L);
     int8_t *tmp = (int8_t *)malloc((size_t)V);
     for (uint64_t s = 0; s < n_sweeps; ++s) {
         uint64_t t = t0 + s;
         for (int k = 0; k < M; ++k) {
             int8_t *Sk = S + (size_t)k * V;
-            for (int colour = 0; colour < 2; ++colour) {
+            for (int colour = 0; colour < ncol; ++colour) {
                 for (int i = 0; i < V; ++i) {
-                    int x = i % L, y = (i / L) % L, zz = (dim == 3) ? i / (L * L) : 0;
-                    if (((x + y + zz) & 1) != colour) continue;
+                    if (or_pt_colour(dim, L, i) != colour) continue;
                     int h = local_field(dim, L, J, Sk, i);
                     int n_unsat = (z - Sk[i] * h) / 2;
                     int dE = 2 * Sk[i] * h;
@@ -457,6 +477,40 @@ int or_pt_sweeps(int dim, int L, uint64_t seed, uint32_t rid, int M, const int8_
     }
     free(tmp);
     return 0;
+}
+
+/* One step of the constant-exchange-rate temperature adaptation (Sec. II, PT: the
+ * exchange rates are imposed on each realization during equilibration by moving its
+ * temperatures; the rule below is this implementation's own).  beta[0..M-1] ascending; the
+ * end points stay.  Pair k (slots k, k+1, gap D_k = beta[k+1] - beta[k]) accepted n_acc[k] of
+ * n_att[k] exchange attempts, rate A_k, clamped to [0.005, 0.995].  Reading the cost
+ * w_k = -ln A_k as proportional to the gap, s_k = w_k / D_k is the pair's stiffness and the
+ * gaps that give every pair the same rate are D*_k = span (1/s_k) / sum_j (1/s_j).  The new
+ * gaps are (1 - eta) D_k + eta D*_k; the betas are their running sums from beta[0].  With a
+ * pair that had no attempt nothing changes.  Equal rates are the fixed point. */
+void or_pt_adapt(int M, double *beta, const uint64_t *n_acc, const uint64_t *n_att, double eta) {
+    if (M < 3) return;
+    for (int k = 0; k + 1 < M; ++k)
+        if (n_att[k] == 0) return;
+    double span = beta[M - 1] - beta[0];
+    double *gap = (double *)malloc(sizeof(double) * (size_t)(M - 1));
+    double *inv_s = (double *)malloc(sizeof(double) * (size_t)(M - 1));
+    double sum = 0.0;
+    for (int k = 0; k + 1 < M; ++k) {
+        double a = (double)n_acc[k] / (double)n_att[k];
+        if (a < 0.005) a = 0.005;
+        if (a > 0.995) a = 0.995;
+        gap[k] = beta[k + 1] - beta[k];
+        inv_s[k] = gap[k] / -log(a);
+        sum += inv_s[k];
+    }
+    /* beta[0] and beta[M-1] stay; the interior points are running sums of the new gaps */
+    for (int k = 0; k + 2 < M; ++k) {
+        double target = span * inv_s[k] / sum;
+        beta[k + 1] = beta[k] + ((1.0 - eta) * gap[k] + eta * target);
+    }
+    free(gap);
+    free(inv_s);
 }
 
 /* ---------------------------------------------------------------- brute force */
