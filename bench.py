@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
-    ap.add_argument("--only", choices=["pt", "uneven", "serving", "recursion"], default=None,
+    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "recursion"], default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--pt-sweeps", type=int, default=200)
     return ap.parse_args()
@@ -328,6 +328,51 @@ def bench_pt(S: int = 200):
             "swap_acceptance_mean": float(swaps.sum() / max(1, (PT["M"] - 1) * PT["n_real"] * (20 + S) / 2))}
 
 
+def bench_pt_protocol(rounds: int = 10, window: int = 400, S: int = 1000):
+    """The paper's PT protocol (Sec. II, PT) on L=8: M=20 replicas per realization, 1024
+    realizations, temperatures adapted per realization towards constant exchange rates
+    (`rounds` windows of `window` sweeps), then S production sweeps timed."""
+    import numpy as np
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    from paper_2011_08560_gb300.workloads import PT, geometric_betas
+    M = 20
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=PT["seed"], device=0, stream=stream.cuda_stream)
+    ctx.pt_init(PT["dim"], PT["L"], PT["n_real"], geometric_betas(M, PT["beta_min"], PT["beta_max"]))
+
+    def rates():
+        acc, att = ctx.pt_exchange_counts()
+        return acc / att[None, :]
+
+    ctx.pt_run(window)
+    r0 = rates()
+    ctx.pt_adapt(0.0)                      # new window, temperatures unchanged
+    for _ in range(rounds):
+        ctx.pt_run(window)
+        ctx.pt_adapt(0.5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.pt_run(S)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    r1 = rates()
+    ctx.close()
+    attempts = PT["n_real"] * M * PT["L"] ** 3 * S
+
+    def summary(r):
+        spread = r.max(axis=1) - r.min(axis=1)
+        return {"mean_rate": float(r.mean()), "median_spread": float(np.median(spread)),
+                "realizations_all_pairs_in_40_60pct": float(np.mean(np.all((r >= 0.4) & (r <= 0.6), axis=1)))}
+
+    return {"workload": f"PT protocol: 3D L=8, {PT['n_real']} realizations x {M} temperatures, "
+                        f"beta in [{PT['beta_min']}, {PT['beta_max']}], {rounds} adaptation windows of "
+                        f"{window} sweeps", "sweeps": S, "ms": ms, "attempts_per_ns": attempts / (ms * 1e6),
+            "exchange_rates_geometric": summary(r0), "exchange_rates_adapted": summary(r1)}
+
+
 def bench_uneven(S: int = 100, iters: int = 3):
     """Uneven batch: 4096 realizations, L uniform over {4,6,8,10,12} (round robin by id), each
     as a power-law, a flat and a 1/k chain, in one persistent launch per step; the
@@ -473,7 +518,8 @@ def main():
         return
 
     if args.only:
-        fn = {"pt": lambda: bench_pt(args.pt_sweeps), "uneven": bench_uneven, "serving": bench_serving,
+        fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
+              "uneven": bench_uneven, "serving": bench_serving,
               "recursion": bench_recursion}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
@@ -486,8 +532,8 @@ def main():
     r = run_gpu(args, rank, world)
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = {"pt": bench_pt(), "uneven": bench_uneven(), "serving": bench_serving(),
-                  "recursion": bench_recursion()}
+        extras = {"pt": bench_pt(), "pt_protocol": bench_pt_protocol(), "uneven": bench_uneven(),
+                  "serving": bench_serving(), "recursion": bench_recursion()}
     if rank != 0:
         if world > 1:
             import torch

@@ -243,20 +243,24 @@ typedef struct {
 } ea_pt_stats;
 
 /* Sets up n_real realizations rid0 .. rid0+n_real-1 (rid0 a multiple of 32; realizations
- * are packed 32 to a word) of an even-L lattice (4 <= L <= 12; the checkerboard needs even L)
- * with M replicas (2 <= M <= 64) at host betas[M] (strictly increasing).  Couplings from the
- * seed (as ea_init_disorder) or from couplings_or_null (int8[n_real][dim*V]); replica k of
- * realization r starts from the random spins of stream k.  Metropolis thresholds
- * floor(exp(-beta_k dE) 2^32) and exchange thresholds floor(exp(-(beta_{k+1}-beta_k) 4d) 2^32)
- * are built on the device.  Replaces any previous PT batch of the context. */
+ * are packed 32 to a word) of lattices of linear size L (3 <= L <= 12) with M replicas
+ * (2 <= M <= 64), every realization at host betas[M] (strictly increasing; pt_set_betas gives
+ * each realization its own set).  Couplings from the seed (as ea_init_disorder) or from
+ * couplings_or_null (int8[n_real][dim*V]); replica k of realization r starts from the random
+ * spins of stream k.  Metropolis thresholds floor(exp(-beta_k dE) 2^32) are built on the
+ * device; exchange thresholds floor(exp(-(beta_{k+1}-beta_k) 4d) 2^32) are evaluated there at
+ * each exchange.  Replaces any previous PT batch of the context. */
 int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, int M, const double *betas,
             const int8_t *couplings_or_null);
 
 /* Round-trip bounds per realization (host int32[n_real] each): bottom E_g, top E_hot. */
 int pt_set_rt_bounds(ea_ctx *ctx, const int32_t *e_g, const int32_t *e_hot);
 
-/* n_sweeps PT sweeps: per sweep, a checkerboard Metropolis sweep of every replica (sites with
- * even coordinate sum first, each colour in lexicographic order), exchanges between slots
+/* n_sweeps PT sweeps: per sweep, a Metropolis sweep of every replica colour class by colour
+ * class, each class in lexicographic order -- even L: the checkerboard (even coordinate sum
+ * first); odd L, where the checkerboard is not a proper colouring under periodic boundaries:
+ * colour (c(x) + c(y) + c(z)) mod 3 with c(x) = x mod 3, except c(L-1) = 1 when L = 1 (mod 3)
+ * -- then exchanges between slots
  * (k, k+1) for k = t mod 2, t mod 2 + 2, ... (accepted if E_{k+1} >= E_k, else with
  * probability exp((beta_{k+1}-beta_k)(E_{k+1}-E_k))), then, if count_roundtrips, one
  * round-trip check per replica.  The random word of an uphill update of realization r at
@@ -274,6 +278,24 @@ int pt_get_roundtrips(ea_ctx *ctx, ea_pt_stats *out, int reset);
 
 /* Accepted exchanges per slot pair (k, k+1), summed over realizations: uint64[M-1]. */
 int pt_get_swap_counts(ea_ctx *ctx, uint64_t *out);
+
+/* f2 -- the paper's PT protocol (Sec. II, PT): constant exchange rates imposed on every
+ * realization during equilibration by moving its temperatures.
+ * pt_set_betas / pt_get_betas: per-realization inverse temperatures, host double[n_real][M],
+ * each row strictly increasing (EA_EINVAL otherwise); setting rebuilds the thresholds.
+ * pt_get_exchange_counts: since pt_init or the last pt_adapt, accepted exchanges of pair
+ * (k, k+1) per realization (uint32[n_real][M-1], may be NULL) and the attempts per pair, the
+ * same for every realization (uint64[M-1], may be NULL: pair k is tried at sweeps t = k mod 2).
+ * pt_adapt: one adaptation step per realization from those counts, then a new count window.
+ * Rate A_k = accepted / attempts clamped to [0.005, 0.995], gap D_k = beta_{k+1} - beta_k,
+ * stiffness s_k = -ln(A_k) / D_k; the gaps that give every pair the same rate are
+ * D*_k = (beta_{M-1} - beta_0) (1/s_k) / sum_j (1/s_j); the new gaps are
+ * (1 - eta) D_k + eta D*_k (0 <= eta <= 1) with beta_0 and beta_{M-1} fixed.  A realization
+ * whose window holds a pair without attempts keeps its temperatures. */
+int pt_set_betas(ea_ctx *ctx, const double *betas);
+int pt_get_betas(ea_ctx *ctx, double *betas);
+int pt_get_exchange_counts(ea_ctx *ctx, uint32_t *accepted, uint64_t *attempted);
+int pt_adapt(ea_ctx *ctx, double eta);
 
 /* ------------------------------------------------------------------ no allocation
  * The paper has no counterpart to this entry point: it serves callers that cannot allocate

@@ -1,22 +1,23 @@
 // pt_kernels.cu -- a6 + a7: parallel tempering (Sec. II, PT; Eq. "temperatureexchange").
 //
 // M replicas of every realization, one per temperature slot k (beta ascending with k, slot
-// 0 hottest).  Each sweep: a checkerboard Metropolis sweep of every slot (sites with even
-// coordinate sum first, then odd), then replica exchange between slots (k, k+1) for
-// k = t mod 2, t mod 2 + 2, ..., then one round-trip check per replica (Sec. III, PT variant:
-// between E_g and an energy typical of a high temperature, E_hot).
+// 0 hottest; every realization has its own temperature set).  Each sweep: a Metropolis sweep
+// of every slot colour class by colour class (even L: the checkerboard, sites with even
+// coordinate sum first; odd L: three colours, see pt_colour), then replica exchange between
+// slots (k, k+1) for k = t mod 2, t mod 2 + 2, ..., then one round-trip check per replica
+// (Sec. III, PT variant: between E_g and an energy typical of a high temperature, E_hot).
 //
 // Layout.  Realizations come in groups of 32 (realization id 32g + b is bit b); the
-// configuration at slot k of a group is one multi-spin-coded word per site, so all 32 bits
-// of a word share one temperature and one set of Metropolis thresholds.  Exchanges move
+// configuration at slot k of a group is one multi-spin-coded word per site.  Exchanges move
 // configurations (not temperatures) with masked XOR swaps of whole words.
 //
 // Acceptance.  For a site word the unsatisfied-bond count of every bit is a bit-sliced sum;
-// bits with dE <= 0 flip.  Each uphill bit b compares its 32-bit random number r_b with the
-// slot's threshold; r_b's bit 31-m is bit b of random word m (Philox4x32-10 of counter
-// (8i + m/4, t, g, 4 | k<<8), word m&3).  The comparison runs over bit planes from the most
-// significant one and stops when every uphill bit is decided, so a site word usually needs
-// a few random words rather than 32.
+// bits with dE <= 0 flip.  Each uphill bit b compares its 32-bit random number r_b with its
+// own threshold (slot k, its realization's beta_k, its class); r_b's bit 31-m is bit b of
+// random word m (Philox4x32-10 of counter (8i + m/4, t, g, 4 | k<<8), word m&3), and the
+// thresholds are stored the same way, as bit planes: plane m of class c holds bit 31-m of
+// the 32 realizations' thresholds.  The comparison runs over planes from the most
+// significant one: the first 8 without branches, the rest only while a bit is undecided.
 //
 // Parallel work.  One thread-block cluster per group: CS CTAs, each owning M/CS consecutive
 // slots in shared memory.  Energies are recomputed after every sweep (bit-sliced counters,
@@ -45,18 +46,19 @@ struct PtRt {
 };
 
 struct PtState {
-    int dim = 0, L = 0, V = 0, nb = 0, M = 0, n_real = 0, n_groups = 0, cs = 1, dmax = 0;
+    int dim = 0, L = 0, V = 0, nb = 0, M = 0, n_real = 0, n_groups = 0, cs = 1;
     uint32_t rid0 = 0;
     uint64_t t = 0;
-    std::vector<double> betas;
+    uint64_t t_win = 0;            // start of the exchange-count window (pt_adapt)
     uint32_t *d_spins = nullptr;   // [g][k][V]
     uint32_t *d_bonds = nullptr;   // [g][nb]
     int32_t *d_E = nullptr;        // [g][k][32]
     int32_t *d_label = nullptr;    // [g][k][32]
     PtRt *d_rt = nullptr;          // [g][label][32]
     int32_t *d_bounds = nullptr;   // [g][32][2] (e_g, e_hot)
-    uint32_t *d_thr_k = nullptr;   // [M][8]
-    uint32_t *d_thr_pair = nullptr;  // [M-1][dmax+1]
+    double *d_beta = nullptr;      // [g][k][32] inverse temperatures
+    uint32_t *d_planes = nullptr;  // [g][k][32 planes][4] Metropolis thresholds (classes 0..2, pad)
+    uint32_t *d_xacc = nullptr;    // [g][k][32] accepted exchanges of pair (k, k+1) in the window
     unsigned long long *d_swaps = nullptr;  // [M-1]
     int *d_err = nullptr;
 };
@@ -101,6 +103,27 @@ __device__ __forceinline__ int pt_nbr(int i, int d, int sgn) {
     return x + L * (y + L * z);
 }
 
+// Colour of a site for the PT sweep.  Even L: (x + y + z) mod 2.  Odd L: the sum of per-axis
+// colours mod 3, an axis position x having colour x mod 3 except the last one (x = L-1) when
+// L = 1 (mod 3), which takes 1 so that it differs from both neighbours L-2 and 0; a step to a
+// neighbour then changes the sum by 1 or 2 (mod 3), so no two neighbours share a colour.
+template <int DIM, int L>
+__device__ __forceinline__ int pt_colour(int i) {
+    const int x = i % L, y = (i / L) % L, z = DIM == 3 ? i / (L * L) : 0;
+    if constexpr ((L & 1) == 0) {
+        return (x + y + z) & 1;
+    } else {
+        auto ax = [](int c) { return (c == L - 1 && (L - 1) % 3 == 0) ? 1 : c % 3; };
+        return (ax(x) + ax(y) + (DIM == 3 ? ax(z) : 0)) % 3;
+    }
+}
+
+__device__ __forceinline__ uint32_t quantize_prob(double p) {
+    if (p >= 1.0) return kAlways;
+    const double q = floor(p * 4294967296.0);
+    return (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
+}
+
 struct PtArgs {
     uint32_t *spins;
     const uint32_t *bonds;
@@ -108,10 +131,11 @@ struct PtArgs {
     int32_t *label;
     PtRt *rt;
     const int32_t *bounds;
-    const uint32_t *thr_k;
-    const uint32_t *thr_pair;
+    const uint32_t *planes;
+    const double *beta;
+    uint32_t *xacc;
     unsigned long long *swaps;
-    int M, spc, dmax, n_real;
+    int M, spc, n_real;
     uint32_t rid0;
     uint64_t t0, n_sweeps;
     int count_rt;
@@ -128,13 +152,15 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
     const int spc = a.spc, k0 = rank * spc, M = a.M;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
+    constexpr int NCOL = (L & 1) ? 3 : 2;
     extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *S = sm;                       // [spc][V]
+    uint4 *P = reinterpret_cast<uint4 *>(sm);  // [spc][32] threshold planes (class 0, 1, 2, pad)
+    uint32_t *S = sm + spc * 128;           // [spc][V]
     uint32_t *J = S + spc * V;              // [NB], J[i*DIM + d]
     int32_t *Es = (int32_t *)(J + NB);      // [spc][32]
     int32_t *Ls = Es + spc * 32;            // [spc][32]
-    uint32_t *Th = (uint32_t *)(Ls + spc * 32);  // [spc][8]
-    uint32_t *Amask = Th + spc * 8;         // [spc] exchange masks of owned pairs
+    uint32_t *Amask = (uint32_t *)(Ls + spc * 32);  // [spc] exchange masks of owned pairs
+    int32_t *Cl = (int32_t *)(Amask + spc); // odd L: sites by colour [V], then offsets [4]
 
     const uint32_t group_rid0 = a.rid0 + 32u * (uint32_t)g;
     const int nvalid = min(32, a.n_real - 32 * g);
@@ -147,7 +173,18 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         Es[k] = a.E[((size_t)g * M + k0) * 32 + k];
         Ls[k] = a.label[((size_t)g * M + k0) * 32 + k];
     }
-    for (int k = tid; k < spc * 8; k += blockDim.x) Th[k] = a.thr_k[k0 * 8 + k];
+    for (int k = tid; k < spc * 128; k += blockDim.x) sm[k] = a.planes[((size_t)g * M + k0) * 128 + k];
+    if constexpr ((L & 1) != 0) {
+        if (tid == 0) {  // colour classes in lexicographic order (a few thousand steps per launch)
+            int n = 0;
+            for (int c = 0; c < NCOL; ++c) {
+                Cl[V + c] = n;
+                for (int i = 0; i < V; ++i)
+                    if (pt_colour<DIM, L>(i) == c) Cl[n++] = i;
+            }
+            Cl[V + NCOL] = n;
+        }
+    }
     __syncthreads();
     cluster.sync();
 
@@ -155,13 +192,18 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         const uint64_t t = a.t0 + s;
         const uint32_t tt = (uint32_t)t;
         // ---- checkerboard Metropolis sweep of every owned slot
-        for (int colour = 0; colour < 2; ++colour) {
-            for (int item = tid; item < spc * HALF; item += blockDim.x) {
-                const int ks = item / HALF, j = item % HALF;
-                const int row = j / (L / 2), xh = j % (L / 2);
-                const int y = row % L, z = DIM == 3 ? row / L : 0;
-                const int x = 2 * xh + ((colour + y + z) & 1);
-                const int i = x + L * row;
+        for (int colour = 0; colour < NCOL; ++colour) {
+            const int nc = ((L & 1) == 0) ? HALF : Cl[V + colour + 1] - Cl[V + colour];
+            for (int item = tid; item < spc * nc; item += blockDim.x) {
+                const int ks = item / nc, j = item % nc;
+                int i;
+                if constexpr ((L & 1) == 0) {
+                    const int row = j / (L / 2), xh = j % (L / 2);
+                    const int y = row % L, z = DIM == 3 ? row / L : 0;
+                    i = 2 * xh + ((colour + y + z) & 1) + L * row;
+                } else {
+                    i = Cl[Cl[V + colour] + j];
+                }
                 uint32_t *Sk = S + ks * V;
                 const uint32_t si = Sk[i];
                 uint32_t u[2 * DIM];
@@ -195,7 +237,7 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                 uint32_t acc = ~up;  // dE <= 0 always accepted
                 uint32_t und = up & valid;
                 const int k = k0 + ks;
-                const uint32_t T0 = Th[ks * 8 + 0], T1 = Th[ks * 8 + 1], T2 = Th[ks * 8 + 2];
+                const uint4 *Pk = P + ks * 32;
                 // the 8 most significant planes come from two independent Philox calls and are
                 // compared without branches; planes 8..31 are drawn only while a bit is still
                 // undecided (about 2^-8 per uphill bit)
@@ -205,9 +247,8 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                 const uint32_t Rm[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
-                    const int sh = 31 - m;
-                    const uint32_t Tm = (C[0] & (0u - ((T0 >> sh) & 1u))) | (C[1] & (0u - ((T1 >> sh) & 1u))) |
-                                        (C[2] & (0u - ((T2 >> sh) & 1u)));
+                    const uint4 q = Pk[m];
+                    const uint32_t Tm = (C[0] & q.x) | (C[1] & q.y) | (C[2] & q.z);
                     acc |= und & ~Rm[m] & Tm;  // r bit 0, threshold bit 1: r < threshold
                     und &= ~(Rm[m] ^ Tm);      // equal bits: still undecided
                 }
@@ -216,9 +257,8 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                     if ((m & 3) == 0)
                         w4 = philox4x32_10(make_uint4((uint32_t)(8 * i + (m >> 2)), tt, c2, c3), a.key);
                     const uint32_t R = uint4_get(w4, m & 3);
-                    const int sh = 31 - m;
-                    const uint32_t Tm = (C[0] & (0u - ((T0 >> sh) & 1u))) | (C[1] & (0u - ((T1 >> sh) & 1u))) |
-                                        (C[2] & (0u - ((T2 >> sh) & 1u)));
+                    const uint4 q = Pk[m];
+                    const uint32_t Tm = (C[0] & q.x) | (C[1] & q.y) | (C[2] & q.z);
                     acc |= und & ~R & Tm;
                     und &= ~(R ^ Tm);
                 }
@@ -265,12 +305,16 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                     if (e1 >= e0) {
                         ok = true;
                     } else {
+                        // Eq. "temperatureexchange" with this realization's beta_k, beta_k+1
                         const int d = (e0 - e1) / 4;
-                        const uint32_t th = (d <= a.dmax) ? a.thr_pair[(size_t)k * (a.dmax + 1) + d] : 0u;
+                        const double b0 = a.beta[((size_t)g * M + k) * 32 + lane];
+                        const double b1 = a.beta[((size_t)g * M + k + 1) * 32 + lane];
+                        const uint32_t th = quantize_prob(exp(-(b1 - b0) * 4.0 * (double)d));
                         const uint4 w = philox4x32_10(make_uint4((uint32_t)k, tt, group_rid0 + lane, 1u), a.key);
                         ok = (th == kAlways) || (w.x < th);
                     }
                     A = __ballot_sync(kFull, ok) & valid;
+                    if ((A >> lane) & 1u) a.xacc[((size_t)g * M + k) * 32 + lane] += 1u;
                     if (lane == 0 && A) atomicAdd(&a.swaps[k], (unsigned long long)__popc(A));
                 }
                 if (lane == 0) Amask[ks] = A;
@@ -408,19 +452,20 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
     a.label = p->d_label;
     a.rt = p->d_rt;
     a.bounds = p->d_bounds;
-    a.thr_k = p->d_thr_k;
-    a.thr_pair = p->d_thr_pair;
+    a.planes = p->d_planes;
+    a.beta = p->d_beta;
+    a.xacc = p->d_xacc;
     a.swaps = p->d_swaps;
     a.M = p->M;
     a.spc = p->M / p->cs;
-    a.dmax = p->dmax;
     a.n_real = p->n_real;
     a.rid0 = p->rid0;
     a.t0 = p->t;
     a.n_sweeps = n_sweeps;
     a.count_rt = count_rt;
     a.key = ctx->key;
-    const size_t smem = (size_t)(a.spc * G::V + G::NB + a.spc * 32 * 2 + a.spc * 8 + a.spc) * 4;
+    const size_t smem = (size_t)(a.spc * 128 + a.spc * G::V + G::NB + a.spc * 32 * 2 + a.spc +
+                                 ((L & 1) ? G::V + 4 : 0)) * 4;
     cudaError_t e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -447,34 +492,79 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
 cudaError_t pt_dispatch(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, uint64_t n_sweeps, int count_rt) {
 #define PT_CASE(D, LL) \
     if (p->dim == D && p->L == LL) return pt_launch_all<D, LL>(p, dJ, ctx, what, n_sweeps, count_rt);
-    PT_CASE(3, 4) PT_CASE(3, 6) PT_CASE(3, 8) PT_CASE(3, 10) PT_CASE(3, 12)
-    PT_CASE(2, 4) PT_CASE(2, 6) PT_CASE(2, 8) PT_CASE(2, 10) PT_CASE(2, 12)
+    PT_CASE(3, 3) PT_CASE(3, 4) PT_CASE(3, 5) PT_CASE(3, 6) PT_CASE(3, 7) PT_CASE(3, 8) PT_CASE(3, 9)
+    PT_CASE(3, 10) PT_CASE(3, 11) PT_CASE(3, 12)
+    PT_CASE(2, 3) PT_CASE(2, 4) PT_CASE(2, 5) PT_CASE(2, 6) PT_CASE(2, 7) PT_CASE(2, 8) PT_CASE(2, 9)
+    PT_CASE(2, 10) PT_CASE(2, 11) PT_CASE(2, 12)
 #undef PT_CASE
     return cudaErrorInvalidValue;
 }
 
-__global__ void pt_tables_kernel(const double *beta, int M, int dim, int dmax, uint32_t *thr_k, uint32_t *thr_pair) {
+// Metropolis threshold planes of every (group, slot): one warp, lane b = realization bit.
+// Class n (n unsatisfied bonds, dE = 2z - 4n > 0) accepts with exp(-beta dE) (Sec. II, PT).
+__global__ void pt_planes_kernel(const double *__restrict__ beta, int dim, uint32_t *__restrict__ planes) {
+    const int gk = blockIdx.x, lane = threadIdx.x;
     const int z = 2 * dim;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    auto quant = [](double p) -> uint32_t {
-        if (p >= 1.0) return kAlways;
-        const double q = floor(p * 4294967296.0);
-        return (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
-    };
-    if (idx < M * 8) {
-        const int k = idx / 8, n = idx % 8;
-        uint32_t v = 0u;
-        if (n <= z) {
-            const int dE = 2 * z - 4 * n;
-            v = (dE <= 0) ? kAlways : quant(exp(-beta[k] * (double)dE));
+    const double b = beta[(size_t)gk * 32 + lane];
+    uint32_t thr[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+        const int dE = 2 * z - 4 * n;
+        thr[n] = (dE <= 0) ? kAlways : quantize_prob(exp(-b * (double)dE));
+    }
+    uint32_t *out = planes + (size_t)gk * 128;
+    for (int m = 0; m < 32; ++m) {
+        const int sh = 31 - m;
+        const uint32_t p0 = __ballot_sync(kFull, (thr[0] >> sh) & 1u);
+        const uint32_t p1 = __ballot_sync(kFull, (thr[1] >> sh) & 1u);
+        const uint32_t p2 = __ballot_sync(kFull, (thr[2] >> sh) & 1u);
+        if (lane == 0) {
+            out[4 * m + 0] = p0;
+            out[4 * m + 1] = p1;
+            out[4 * m + 2] = p2;
+            out[4 * m + 3] = 0u;
         }
-        thr_k[idx] = v;
     }
-    const int np = (M - 1) * (dmax + 1);
-    if (idx < np) {
-        const int k = idx / (dmax + 1), d = idx % (dmax + 1);
-        thr_pair[idx] = (d == 0) ? kAlways : quant(exp(-(beta[k + 1] - beta[k]) * 4.0 * (double)d));
+}
+
+constexpr int kMaxSlots = 64;
+
+// One step of the constant-exchange-rate adaptation (Sec. II, PT: the temperatures of every
+// realization are moved during equilibration until its exchange rates are equal).  One thread
+// per realization.  Pair k accepted xacc of att_k attempts in the window: rate A_k clamped to
+// [0.005, 0.995], stiffness s_k = -ln A_k / D_k of its gap D_k; the gaps that equalise the rates
+// are D*_k = span (1/s_k) / sum_j (1/s_j); new gaps (1 - eta) D_k + eta D*_k, end points fixed.
+// A pair without attempts leaves the realization unchanged.  Counts of the window are cleared.
+__global__ void pt_adapt_kernel(double *__restrict__ beta, uint32_t *__restrict__ xacc, int M, int n_real,
+                                uint64_t t0, uint64_t t1, double eta) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_real) return;
+    const size_t g = r / 32, b = r % 32;
+    auto at = [&](int k) -> size_t { return (g * M + k) * 32 + b; };
+    bool ok = M >= 3;
+    double inv_s[kMaxSlots], gap[kMaxSlots];
+    double sum = 0.0;
+    for (int k = 0; k + 1 < M; ++k) {
+        const uint64_t first = t0 + (uint64_t)(((uint64_t)k - t0) & 1u);  // first t >= t0, t = k (mod 2)
+        const uint64_t att = (first >= t1) ? 0 : (t1 - 1 - first) / 2 + 1;
+        if (att == 0) ok = false;
+        if (!ok) break;
+        double a = (double)xacc[at(k)] / (double)att;
+        a = a < 0.005 ? 0.005 : (a > 0.995 ? 0.995 : a);
+        gap[k] = __dsub_rn(beta[at(k + 1)], beta[at(k)]);
+        inv_s[k] = gap[k] / -log(a);
+        sum = __dadd_rn(sum, inv_s[k]);
     }
+    if (ok) {
+        const double span = __dsub_rn(beta[at(M - 1)], beta[at(0)]);
+        double bk = beta[at(0)];
+        for (int k = 0; k + 2 < M; ++k) {
+            const double target = __dmul_rn(span, inv_s[k]) / sum;
+            bk = __dadd_rn(bk, __dadd_rn(__dmul_rn(__dsub_rn(1.0, eta), gap[k]), __dmul_rn(eta, target)));
+            beta[at(k + 1)] = bk;
+        }
+    }
+    for (int k = 0; k < M; ++k) xacc[at(k)] = 0u;
 }
 
 }  // namespace
@@ -483,7 +573,7 @@ void pt_release(ea_ctx *ctx) {
     if (!ctx || !ctx->pt) return;
     PtState *p = ctx->pt;
     void *ptrs[] = {p->d_spins, p->d_bonds, p->d_E, p->d_label, p->d_rt, p->d_bounds,
-                    p->d_thr_k, p->d_thr_pair, p->d_swaps, p->d_err};
+                    p->d_beta, p->d_planes, p->d_xacc, p->d_swaps, p->d_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -496,11 +586,30 @@ void pt_release(ea_ctx *ctx) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
     } while (0)
 
+// host betas [n_real][M] -> device [g][k][32] (bits past n_real copy the group's first
+// realization), then the threshold planes
+static int pt_upload_betas(ea_ctx *ctx, const double *betas) {
+    PtState *p = ctx->pt;
+    const size_t G = p->n_groups, M = p->M;
+    std::vector<double> h(G * M * 32);
+    for (size_t g = 0; g < G; ++g)
+        for (size_t k = 0; k < M; ++k)
+            for (size_t b = 0; b < 32; ++b) {
+                const size_t r = (32 * g + b < (size_t)p->n_real) ? 32 * g + b : 32 * g;
+                h[(g * M + k) * 32 + b] = betas[r * M + k];
+            }
+    PT_CUDA(cudaMemcpyAsync(p->d_beta, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    pt_planes_kernel<<<(int)(G * M), 32, 0, ctx->stream>>>(p->d_beta, p->dim, p->d_planes);
+    PT_CUDA(cudaGetLastError());
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
 extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, int M, const double *betas,
                        const int8_t *couplings_or_null) {
     if (!ctx) return fail(EA_EINVAL, "null context");
     if (dim != 2 && dim != 3) return fail(EA_EINVAL, "dim must be 2 or 3");
-    if (L < 4 || L > 12 || (L & 1)) return fail(EA_EINVAL, "PT needs an even L in [4, 12] (checkerboard)");
+    if (L < 3 || L > 12) return fail(EA_EINVAL, "PT needs L in [3, 12]");
     if (n_real <= 0) return fail(EA_EINVAL, "n_real must be positive");
     if (rid0 % 32) return fail(EA_EINVAL, "rid0 must be a multiple of 32 (realizations are packed 32 per word)");
     if (M < 2 || M > 64) return fail(EA_EINVAL, "M must be in [2, 64]");
@@ -519,8 +628,6 @@ extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, i
     p->n_real = n_real;
     p->n_groups = (n_real + 31) / 32;
     p->rid0 = rid0;
-    p->dmax = p->nb / 2;
-    p->betas.assign(betas, betas + M);
     p->cs = 1;
     for (int c : {8, 4, 2})  // 16-CTA clusters measured slower
         if (M % c == 0) { p->cs = c; break; }
@@ -534,23 +641,22 @@ extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, i
     if ((rc = alloc((void **)&p->d_spins, G * M * p->V * 4)) || (rc = alloc((void **)&p->d_bonds, G * p->nb * 4)) ||
         (rc = alloc((void **)&p->d_E, G * M * 32 * 4)) || (rc = alloc((void **)&p->d_label, G * M * 32 * 4)) ||
         (rc = alloc((void **)&p->d_rt, G * M * 32 * sizeof(PtRt))) ||
-        (rc = alloc((void **)&p->d_bounds, G * 32 * 2 * 4)) || (rc = alloc((void **)&p->d_thr_k, M * 8 * 4)) ||
-        (rc = alloc((void **)&p->d_thr_pair, (size_t)(M - 1) * (p->dmax + 1) * 4)) ||
+        (rc = alloc((void **)&p->d_bounds, G * 32 * 2 * 4)) || (rc = alloc((void **)&p->d_beta, G * M * 32 * 8)) ||
+        (rc = alloc((void **)&p->d_planes, G * M * 128 * 4)) || (rc = alloc((void **)&p->d_xacc, G * M * 32 * 4)) ||
         (rc = alloc((void **)&p->d_swaps, (M - 1) * 8)) || (rc = alloc((void **)&p->d_err, 4))) {
         pt_release(ctx);
         return rc;
     }
-    // tables (FP64 exp -> u32), bounds default: never reached
+    // the same temperatures for every realization; bounds default: never reached
+    std::vector<double> hbeta((size_t)n_real * M);
+    for (int r = 0; r < n_real; ++r)
+        for (int k = 0; k < M; ++k) hbeta[(size_t)r * M + k] = betas[k];
+    if ((rc = pt_upload_betas(ctx, hbeta.data()))) return rc;
     void *scr;
-    if ((rc = ctx_scratch(ctx, (size_t)M * 8 + (size_t)n_real * p->nb + 256, &scr))) return rc;
-    double *d_beta = (double *)scr;
-    PT_CUDA(cudaMemcpyAsync(d_beta, betas, M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    const int ntab = std::max(M * 8, (M - 1) * (p->dmax + 1));
-    pt_tables_kernel<<<(ntab + 255) / 256, 256, 0, ctx->stream>>>(d_beta, M, dim, p->dmax, p->d_thr_k, p->d_thr_pair);
-    PT_CUDA(cudaGetLastError());
     const int8_t *dJ = nullptr;
     if (couplings_or_null) {
-        dJ = (const int8_t *)((char *)scr + (((size_t)M * 8 + 127) & ~(size_t)127));
+        if ((rc = ctx_scratch(ctx, (size_t)n_real * p->nb + 256, &scr))) return rc;
+        dJ = (const int8_t *)scr;
         PT_CUDA(cudaMemcpyAsync((void *)dJ, couplings_or_null, (size_t)n_real * p->nb, cudaMemcpyHostToDevice,
                                 ctx->stream));
     }
@@ -580,6 +686,64 @@ extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, i
     PT_CUDA(cudaMemcpyAsync(p->d_rt, hr.data(), hr.size() * sizeof(PtRt), cudaMemcpyHostToDevice, ctx->stream));
     PT_CUDA(cudaStreamSynchronize(ctx->stream));
     p->t = 0;
+    p->t_win = 0;
+    return EA_OK;
+}
+
+extern "C" int pt_set_betas(ea_ctx *ctx, const double *betas) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    if (!betas) return fail(EA_EINVAL, "null betas");
+    const PtState *p = ctx->pt;
+    for (int r = 0; r < p->n_real; ++r)
+        for (int k = 0; k + 1 < p->M; ++k)
+            if (!(betas[(size_t)r * p->M + k + 1] > betas[(size_t)r * p->M + k]))
+                return fail(EA_EINVAL, "betas of realization %d must increase with the slot index", r);
+    return pt_upload_betas(ctx, betas);
+}
+
+extern "C" int pt_get_betas(ea_ctx *ctx, double *betas) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    if (!betas) return fail(EA_EINVAL, "null output");
+    const PtState *p = ctx->pt;
+    const size_t G = p->n_groups, M = p->M;
+    std::vector<double> h(G * M * 32);
+    PT_CUDA(cudaMemcpyAsync(h.data(), p->d_beta, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < p->n_real; ++r)
+        for (size_t k = 0; k < M; ++k) betas[(size_t)r * M + k] = h[((r / 32) * M + k) * 32 + r % 32];
+    return EA_OK;
+}
+
+extern "C" int pt_get_exchange_counts(ea_ctx *ctx, uint32_t *accepted, uint64_t *attempted) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    const PtState *p = ctx->pt;
+    const size_t G = p->n_groups, M = p->M;
+    if (accepted) {
+        std::vector<uint32_t> h(G * M * 32);
+        PT_CUDA(cudaMemcpyAsync(h.data(), p->d_xacc, h.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        PT_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int r = 0; r < p->n_real; ++r)
+            for (size_t k = 0; k + 1 < M; ++k) accepted[(size_t)r * (M - 1) + k] = h[((r / 32) * M + k) * 32 + r % 32];
+    }
+    if (attempted)
+        for (size_t k = 0; k + 1 < M; ++k) {
+            const uint64_t first = p->t_win + ((k - p->t_win) & 1u);
+            attempted[k] = (first >= p->t) ? 0 : (p->t - 1 - first) / 2 + 1;
+        }
+    return EA_OK;
+}
+
+extern "C" int pt_adapt(ea_ctx *ctx, double eta) {
+    if (!ctx || !ctx->pt) return fail(EA_ESTATE, "call pt_init first");
+    if (!(eta >= 0.0 && eta <= 1.0)) return fail(EA_EINVAL, "eta must be in [0, 1]");
+    PtState *p = ctx->pt;
+    pt_adapt_kernel<<<(p->n_real + 127) / 128, 128, 0, ctx->stream>>>(p->d_beta, p->d_xacc, p->M, p->n_real,
+                                                                       p->t_win, p->t, eta);
+    PT_CUDA(cudaGetLastError());
+    pt_planes_kernel<<<p->n_groups * p->M, 32, 0, ctx->stream>>>(p->d_beta, p->dim, p->d_planes);
+    PT_CUDA(cudaGetLastError());
+    PT_CUDA(cudaStreamSynchronize(ctx->stream));
+    p->t_win = p->t;
     return EA_OK;
 }
 

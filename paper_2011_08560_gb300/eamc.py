@@ -89,6 +89,10 @@ SIGNATURES = {
     "pt_get_state": (_i, [P, P, P, P, P]),
     "pt_get_roundtrips": (_i, [P, P, _i]),
     "pt_get_swap_counts": (_i, [P, P]),
+    "pt_set_betas": (_i, [P, P]),
+    "pt_get_betas": (_i, [P, P]),
+    "pt_get_exchange_counts": (_i, [P, P, P]),
+    "pt_adapt": (_i, [P, ctypes.c_double]),
 }
 
 _lib = None
@@ -334,3 +338,26 @@ class Context:
         out = np.zeros(M - 1, dtype=np.uint64)
         check(lib().pt_get_swap_counts(self._h, _p(out)))
         return out
+
+    # f2: per-realization temperatures and the constant-exchange-rate adaptation
+    def pt_set_betas(self, betas):
+        dim, L, n, M = self._pt
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        assert b.shape == (n, M)
+        check(lib().pt_set_betas(self._h, _p(b)))
+
+    def pt_betas(self):
+        dim, L, n, M = self._pt
+        out = np.zeros((n, M), dtype=np.float64)
+        check(lib().pt_get_betas(self._h, _p(out)))
+        return out
+
+    def pt_exchange_counts(self):
+        dim, L, n, M = self._pt
+        acc = np.zeros((n, M - 1), dtype=np.uint32)
+        att = np.zeros(M - 1, dtype=np.uint64)
+        check(lib().pt_get_exchange_counts(self._h, _p(acc), _p(att)))
+        return acc, att
+
+    def pt_adapt(self, eta: float = 0.5):
+        check(lib().pt_adapt(self._h, eta))

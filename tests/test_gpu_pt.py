@@ -23,11 +23,13 @@ def eamc():
     return m
 
 
-def _compare(orc, ctx, dim, L, n, betas, sweeps_list, e_g, e_hot, rid0=0, J=None):
-    M = len(betas)
-    V = L ** dim
-    reals = [orc.PTRealization(dim, L, SEED, rid0 + r, betas, J=None if J is None else J[r])
-             for r in range(n)]
+def _compare(orc, ctx, dim, L, n, betas, sweeps_list, e_g, e_hot, rid0=0, J=None, reals=None):
+    """betas: one list for every realization, or an array [n][M] of per-realization sets."""
+    per = np.ndim(betas) == 2
+    M = np.shape(betas)[-1]
+    if reals is None:
+        reals = [orc.PTRealization(dim, L, SEED, rid0 + r, betas[r] if per else betas,
+                                   J=None if J is None else J[r]) for r in range(n)]
     ctx.pt_set_rt_bounds(np.full(n, e_g, np.int32), np.full(n, e_hot, np.int32))
     for sw in sweeps_list:
         ctx.pt_run(sw, count_roundtrips=True)
@@ -52,6 +54,11 @@ def _compare(orc, ctx, dim, L, n, betas, sweeps_list, e_g, e_hot, rid0=0, J=None
 
 @pytest.mark.parametrize("dim,L,n,betas,sweeps,eg,ehot", [
     (2, 4, 40, [0.2, 0.5, 0.9, 1.4], [60, 90], -20, -8),
+    (3, 3, 40, [0.2, 0.4, 0.7, 1.1, 1.6, 2.2, 3.0], [50, 30], -40, -16),       # odd L: 3 colours
+    (3, 5, 33, list(np.geomspace(0.25, 3.0, 12)), [12, 9], -180, -80),
+    (2, 5, 35, [0.3, 0.8, 1.5], [40], -40, -15),
+    (3, 7, 3, [0.3, 0.6, 1.0, 1.5, 2.2], [4, 3], -500, -200),
+    (2, 3, 9, [0.4, 1.2], [30], -10, -2),
     (3, 4, 33, [0.25, 0.4, 0.6, 0.8, 1.0, 1.2, 1.5, 1.9], [30, 20], -90, -40),
     (3, 6, 5, list(np.geomspace(0.2, 3.0, 32)), [6, 4], -300, -150),
     (3, 8, 3, [0.3, 0.9, 1.6, 2.4], [3, 2], -700, -300),
@@ -80,7 +87,7 @@ def test_pt_errors(eamc):
     with pytest.raises(eamc.EamcError):
         ctx.pt_run(1)                                   # no PT batch
     with pytest.raises(eamc.EamcError):
-        ctx.pt_init(3, 5, 4, [0.1, 0.2])                # odd L: no checkerboard
+        ctx.pt_init(3, 13, 4, [0.1, 0.2])               # L out of range
     with pytest.raises(eamc.EamcError):
         ctx.pt_init(3, 4, 4, [0.5, 0.2])                # betas not increasing
     with pytest.raises(eamc.EamcError):
@@ -101,3 +108,41 @@ def test_pt_full_size_sampled(eamc, orc):
         p.sweeps(3)
         assert np.array_equal(E[rid], p.E) and np.array_equal(lab[rid], p.label)
         assert np.array_equal(S[rid].reshape(-1), p.S)
+
+
+def test_pt_per_realization_temperatures(eamc, orc):
+    dim, L, n, M = 3, 4, 45, 6
+    rng = np.random.default_rng(3)
+    betas = np.sort(rng.uniform(0.15, 2.5, size=(n, M)), axis=1)
+    ctx = eamc.Context(seed=SEED)
+    ctx.pt_init(dim, L, n, betas[0])
+    ctx.pt_set_betas(betas)
+    assert np.array_equal(ctx.pt_betas(), betas)
+    _compare(orc, ctx, dim, L, n, betas, [40, 25], -90, -40)
+    with pytest.raises(eamc.EamcError):
+        ctx.pt_set_betas(betas[:, ::-1].copy())          # not increasing
+
+
+@pytest.mark.parametrize("dim,L,n,M", [(3, 4, 37, 7), (3, 5, 6, 12), (2, 6, 33, 5)])
+def test_pt_adaptation_parity(eamc, orc, dim, L, n, M):
+    """Counts bit-exact, adapted temperatures to 1e-12, and the runs after each step bit-exact."""
+    betas0 = np.geomspace(0.2, 2.8, M)
+    ctx = eamc.Context(seed=SEED)
+    ctx.pt_init(dim, L, n, betas0)
+    reals = [orc.PTRealization(dim, L, SEED, r, betas0) for r in range(n)]
+    for step, (sw, eta) in enumerate([(61, 0.5), (40, 0.7), (33, 0.3)]):
+        reals = _compare(orc, ctx, dim, L, n, betas0, [sw], -10 ** 6, 10 ** 6, reals=reals)
+        acc, att = ctx.pt_exchange_counts()
+        for r, p in enumerate(reals):
+            a, t = p.window_rates()
+            assert np.array_equal(acc[r], a.astype(np.uint32)), (step, r)
+            assert np.array_equal(att, t)
+        ctx.pt_adapt(eta)
+        for p in reals:
+            p.adapt(eta)
+        got = ctx.pt_betas()
+        for r, p in enumerate(reals):
+            np.testing.assert_allclose(got[r], p.betas, rtol=1e-12, atol=0)
+            assert got[r][0] == betas0[0] and got[r][-1] == betas0[-1]
+        assert not ctx.pt_exchange_counts()[0].any()
+    assert any(not np.allclose(p.betas, betas0) for p in reals)
