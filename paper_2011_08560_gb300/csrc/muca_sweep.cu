@@ -31,6 +31,8 @@ namespace eamc {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kWarps = 4;                 // consumer, bond sums, two random-number warps
+constexpr int kThreads = 32 * kWarps;
 
 template <int L>
 using RowT = typename std::conditional<(L <= 8), uint32_t, uint64_t>::type;
@@ -104,11 +106,12 @@ __device__ __forceinline__ void get4(const uint4 *slots, int q, int lane, T &a, 
     }
 }
 
-// Two warps per tile.  Warp 1 (producer) works one row ahead of warp 0 (consumer): it draws
-// the row's random words and sums, per site, the unsatisfied-bond indicators of the bonds that
-// cannot change while the consumer sweeps that row.  The consumer adds the bond to the row
-// it has just finished (-y) and runs the sequential accept / reject chain.  A block barrier
-// per row hands over a double-buffered record.
+// Four warps per tile.  Warps 1..3 (producers) work one row ahead of warp 0 (consumer): warp
+// 1 sums, per site, the unsatisfied-bond indicators of the bonds that cannot change while the
+// consumer sweeps that row; warps 2 and 3 draw the row's random words (Philox calls g = 2, 3
+// mod 2).  The consumer adds the bond to the row it has just finished (-y) and runs the
+// sequential accept / reject chain.  A block barrier per row hands over a double-buffered
+// record.
 template <int DIM, int L>
 __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotState *__restrict__ slots,
                                            uint32_t *__restrict__ spins,
@@ -121,8 +124,8 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     constexpr int NR = G::NR;
     constexpr T NIB = nib_mask<T, L>();
     constexpr T LASTNIB = T(1) << (4 * (L - 1));
-    const int lane = threadIdx.x & 31;
-    const bool producer = threadIdx.x >= 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool producer = warp >= 1;
 
     // ---- stage the lattice as nibble-packed row words, lane-interleaved: word k of lane l
     //      at [k*32 + l].  Nibble x of a row word is site x of that row.
@@ -135,7 +138,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
     const uint32_t *gsp = spins + td.spin_off;
     const uint32_t *gbd = bonds + td.bond_off;
-    for (int row = producer ? 1 : 0; row < NR; row += 2) {
+    for (int row = warp; row < NR; row += kWarps) {
         T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
         for (int x = 0; x < L; ++x) {
@@ -164,7 +167,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     const char *tab;
     if constexpr (G::SMEM_THR) {
         uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);
-        if (producer) {
+        if (warp == 1) {
             const uint4 *src = reinterpret_cast<const uint4 *>(thr + lrow * 8);
             for (int b = 0; b < G::B; ++b) {
                 const uint4 a = src[2 * b], c = src[2 * b + 1];
@@ -184,9 +187,17 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     const uint64_t t0 = ss.t;
     const uint64_t total = n_sweeps * (uint64_t)NR;  // rows to sweep
 
-    // producer: record of row `row` (sweep index tt) into buffer `k`
+    // producers: record of row `row` (sweep index tt) into buffer `k`
     auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
         uint4 *buf = hand + k * G::HQ * 32;
+        if (warp >= 2) {  // random words of the row's sites: Philox call g covers x = 4g .. 4g+3
+            const uint32_t c3 = ss.stream << 8;
+#pragma unroll
+            for (int g = warp - 2; g < G::NG; g += 2)
+                buf[(G::SUMQ + g) * 32 + lane] =
+                    philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
+            return;
+        }
         const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
         const T R = Rs[row * 32 + lane];
         const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * 32 + lane];
@@ -210,11 +221,6 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         const T wbit = (u_xp >> (4 * (L - 1))) & T(1);
         const T sB = ((stable + (u_xm ^ NIB)) & ~T(0xF)) | (wbit << 3);
         put4<T>(buf, 0, lane, sA, sB, R, jym);
-        const uint32_t c3 = ss.stream << 8;
-#pragma unroll
-        for (int g = 0; g < G::NG; ++g)
-            buf[(G::SUMQ + g) * 32 + lane] =
-                philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
     };
 
     __syncthreads();
@@ -230,7 +236,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             __syncthreads();
             if (k + 1 < total) produce(row, y, z, (uint32_t)(t0 + s), (int)((k + 1) & 1));
         }
-        return;  // both warps pass exactly 1 + total block barriers
+        return;  // every warp passes exactly 1 + total block barriers
     }
 
     // ---- consumer
@@ -261,7 +267,10 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         }
         const int wbit = (int)((sB >> 3) & 1u);
         T accN = 0;   // nibble x = 1 if this chain flipped site x of the row
-        int prow[L];  // row offset after each attempt (measurement at the row end)
+        // measurement after every attempt, off the accept / reject chain: the lowest row
+        // offset of the row and which attempts ended at or above E_top / at or below E_g
+        int lo = 0x7FFFFFFF, plast = 0;
+        uint32_t mtop = 0u, mbot = 0u;
         // software pipeline: iteration x resolves attempt x from acc(x-1), issues both
         // candidate threshold loads of attempt x+1 (they need only acc(x-1)), then compares
         int nA = (int)(sA & 0xF), nB = nA;
@@ -286,7 +295,11 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
             const bool acc = active && (th == kAlways || r < th);
             accN |= T(acc ? 1u : 0u) << (4 * x);
-            prow[x] = acc ? rx + dx : rx;
+            const int pr = acc ? rx + dx : rx;
+            lo = min(lo, pr);
+            mtop |= (uint32_t)(pr >= topB) << x;
+            mbot |= (uint32_t)(pr <= botB) << x;
+            plast = pr;
             rq = rx;
             dq = dx;
             pa = acc ? 1 : 0;
@@ -294,23 +307,21 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         const T Rfin = R ^ accN;
         Rs[row * 32 + lane] = Rfin;
         Rprev = Rfin;
-        // lowest energy and round trips: row minimum / maximum, exact replay only when the
-        // round-trip state can change within this row (rare)
-        int lo = prow[0], hi = prow[0];
-#pragma unroll
-        for (int x = 1; x < L; ++x) { lo = min(lo, prow[x]); hi = max(hi, prow[x]); }
         pmin = min(pmin, lo);
-        pnow = prow[L - 1];
-        if (count_rt && active && ((phase == 1) ? (lo <= botB) : (hi >= topB))) {
+        pnow = plast;
+        // round trips (Sec. III): the attempts of this row in order; a transition happens at
+        // the first attempt that meets the current phase's condition (E <= E_g heading down,
+        // E >= E_top otherwise), the next one is looked for after it (rare: a few rows a sweep)
+        if (count_rt && active && ((phase == 1) ? mbot : mtop) != 0u) {
             const int64_t t = (int64_t)(t0 + s);
-#pragma unroll
-            for (int x = 0; x < L; ++x) {
-                const bool trig = (phase == 1) ? (prow[x] <= botB) : (prow[x] >= topB);
-                if (trig) {
-                    if (phase == 0) { tf = t; phase = 1; }
-                    else if (phase == 1) { phase = 2; }
-                    else { nrt += 1; tl = t; phase = 1; }
-                }
+            int x0 = 0;
+            while (x0 < L) {
+                const uint32_t m = ((phase == 1) ? mbot : mtop) >> x0;
+                if (m == 0u) break;
+                x0 += __ffs(m);  // one past the attempt that meets the condition
+                if (phase == 0) { tf = t; phase = 1; }
+                else if (phase == 1) { phase = 2; }
+                else { nrt += 1; tl = t; phase = 1; }
             }
         }
         if (++y == L) y = 0;
@@ -318,7 +329,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             row = 0;
             y = 0;
             ++s;
-            if (active) hist_l[pnow / RSB] += 1u;
+            if (active) atomicAdd(&hist_l[pnow / RSB], 1u);  // no return value: no wait
         }
     }
     __syncwarp();
@@ -343,7 +354,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     slots[slot] = ss;
 }
 
-// Two warps (consumer + producer) per tile of 32 chains; the tile's L selects the body.
+// Four warps (consumer + producers) per tile of 32 chains; the tile's L selects the body.
 // Direct mode (queue == nullptr): block b sweeps tile tile_list[b] (or b).  Persistent mode:
 // a grid sized to the resident capacity pulls positions of tile_list (longest tiles first)
 // from the counter *queue until n_work positions are taken.
@@ -368,7 +379,7 @@ __device__ __forceinline__ void sweep_one(const TileDesc *__restrict__ tiles, in
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(64, 1)
+__global__ void __launch_bounds__(kThreads, 1)
 muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ tile_list, int n_work,
                   int *__restrict__ queue, SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
                   const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
@@ -388,7 +399,7 @@ muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict_
         if (pos >= n_work) break;
         sweep_one<DIM>(tiles, tile_list[pos], slots, spins, bonds, thr, hist, n_sweeps, key, count_rt,
                        smem_raw);
-        __syncthreads();  // both warps are done with this tile's shared memory
+        __syncthreads();  // every warp is done with this tile's shared memory
     }
 }
 
@@ -437,10 +448,10 @@ cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, i
     }
     if ((e = prepare_sweeps(dim, smem)) != cudaSuccess) return e;
     if (dim == 3) {
-        muca_sweep_kernel<3><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
+        muca_sweep_kernel<3><<<n_blocks, kThreads, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
                                                          d_bonds, d_thr, d_hist, n_sweeps, key, count_rt);
     } else {
-        muca_sweep_kernel<2><<<n_blocks, 64, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
+        muca_sweep_kernel<2><<<n_blocks, kThreads, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
                                                          d_bonds, d_thr, d_hist, n_sweeps, key, count_rt);
     }
     return cudaGetLastError();
@@ -449,9 +460,9 @@ cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, i
 int sweep_blocks_per_sm(int dim, size_t smem) {
     int nb = 0;
     if (dim == 3)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, muca_sweep_kernel<3>, 64, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, muca_sweep_kernel<3>, kThreads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, muca_sweep_kernel<2>, 64, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, muca_sweep_kernel<2>, kThreads, smem);
     return nb > 0 ? nb : 1;
 }
 

@@ -629,7 +629,9 @@ extern "C" int pt_init(ea_ctx *ctx, int dim, int L, int n_real, uint32_t rid0, i
     p->n_groups = (n_real + 31) / 32;
     p->rid0 = rid0;
     p->cs = 1;
-    for (int c : {8, 4, 2})  // 16-CTA clusters measured slower
+    // the largest cluster (at most 8 CTAs: 16-CTA clusters measured slower) that splits the
+    // slots evenly, for the most CTAs per realization group
+    for (int c = 8; c >= 2; --c)
         if (M % c == 0) { p->cs = c; break; }
     const size_t G = p->n_groups;
     auto alloc = [&](void **ptr, size_t bytes) -> int {
