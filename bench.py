@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
-    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "recursion"], default=None,
+    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "recursion", "scan"],
+                    default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--pt-sweeps", type=int, default=200)
     return ap.parse_args()
@@ -328,7 +329,7 @@ def bench_pt(S: int = 200):
             "swap_acceptance_mean": float(swaps.sum() / max(1, (PT["M"] - 1) * PT["n_real"] * (20 + S) / 2))}
 
 
-def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 1000):
+def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 4000):
     """The paper's PT protocol (Sec. II, PT) on L=8: M=20 replicas per realization, 1024
     realizations, T_max = 3.33 (above 3, as the paper requires) down to T_min = 0.465 (the paper
     gives none: chosen so that 20 replicas give exchange rates near its 40-60 % band),
@@ -346,10 +347,10 @@ def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 1000):
 
     def rates():
         acc, att = ctx.pt_exchange_counts()
-        return acc / att[None, :]
+        return acc / att[None, :], att
 
     ctx.pt_run(window)
-    r0 = rates()
+    r0, _ = rates()
     ctx.pt_adapt(0.0)                      # new window, temperatures unchanged
     for _ in range(rounds):
         ctx.pt_run(window)
@@ -360,8 +361,13 @@ def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 1000):
     e1.record(stream)
     stream.synchronize()
     ms = e0.elapsed_time(e1)
-    r1 = rates()
+    r1, att1 = rates()
     ctx.close()
+    # spread that counting noise alone gives equal true rates (each realization's mean rate)
+    rng = np.random.default_rng(0)
+    pm = r1.mean(axis=1, keepdims=True)
+    sim = rng.binomial(att1[None, :].astype(np.int64), np.repeat(pm, M - 1, axis=1)) / att1[None, :]
+    noise_spread = float(np.median(sim.max(axis=1) - sim.min(axis=1)))
     attempts = PT["n_real"] * M * PT["L"] ** 3 * S
 
     def summary(r):
@@ -372,7 +378,8 @@ def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 1000):
     return {"workload": f"PT protocol: 3D L=8, {PT['n_real']} realizations x {M} temperatures, "
                         f"beta in [{beta_min}, {beta_max}], {rounds} adaptation windows of "
                         f"{window} sweeps", "sweeps": S, "ms": ms, "attempts_per_ns": attempts / (ms * 1e6),
-            "exchange_rates_geometric": summary(r0), "exchange_rates_adapted": summary(r1)}
+            "exchange_rates_geometric": summary(r0), "exchange_rates_adapted": summary(r1),
+            "adapted_spread_from_counting_noise_alone": noise_spread}
 
 
 def bench_uneven(S: int = 100, iters: int = 3):
@@ -468,6 +475,32 @@ def bench_recursion(L: int = 8, n: int = 256, iters: int = 24, S: int = 2000, P:
     return out
 
 
+def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 30, dos_sweeps: int = 2000,
+                       prod_sweeps: int = 20000):
+    """Profile-parameter scan (Sec. II): power-law alpha x Delta E grid, flat and 1/k beside
+    it, n_real realizations of L^3, density of states once per realization (flat chains,
+    Berg's recursion), production with round-trip counting in one batched launch.  Reports the
+    mean round-trip time per ensemble and its ratio to flat (jackknife over realizations)."""
+    import time
+
+    import torch
+
+    from paper_2011_08560_gb300 import eamc, scan
+    alphas, poles = (-1.5, -2.5, -3.6, -5.0), (24.0, 48.0, 96.0, 192.0)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    res = scan.profile_scan(3, L, n_real, alphas, poles, seed=6, dos_iters=dos_iters,
+                            dos_sweeps=dos_sweeps, prod_sweeps=prod_sweeps,
+                            recursion=eamc.EA_REC_BERG, stream=stream.cuda_stream)
+    wall = time.perf_counter() - t0
+    rows = res.summary()
+    return {"workload": f"3D L={L}, {n_real} realizations (seed 6), power law alpha in {list(alphas)} x "
+                        f"Delta E in {list(poles)}, flat and 1/k; density of states {dos_iters} x "
+                        f"{dos_sweeps} sweeps (Berg), {prod_sweeps} production sweeps",
+            "wall_s": wall, "best_power_law": res.best(),
+            "ensembles": {r["ensemble"]: {k: v for k, v in r.items() if k != "ensemble"} for r in rows}}
+
+
 def bench_serving(window_s: float = 4.0, drain_s: float = 20.0):
     """Serving: Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12}, round-trip
     targets log-uniform in [10, 1000]; device-resident state, memory-based admission."""
@@ -521,7 +554,7 @@ def main():
 
     if args.only:
         fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
-              "uneven": bench_uneven, "serving": bench_serving,
+              "uneven": bench_uneven, "serving": bench_serving, "scan": bench_profile_scan,
               "recursion": bench_recursion}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
@@ -535,7 +568,7 @@ def main():
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {"pt": bench_pt(), "pt_protocol": bench_pt_protocol(), "uneven": bench_uneven(),
-                  "serving": bench_serving(), "recursion": bench_recursion()}
+                  "serving": bench_serving(), "recursion": bench_recursion(), "scan": bench_profile_scan()}
     if rank != 0:
         if world > 1:
             import torch

@@ -201,6 +201,15 @@ int muca_build_ensemble(ea_ctx *ctx, int chain0, int n, int kind, double alpha,
 int ea_reset_chains(ea_ctx *ctx, const int32_t *chains, int n, const uint32_t *rids,
                     const uint32_t *streams);
 
+/* f4 -- for k < n, chain dst[k] takes chain src[k]'s ln W row, ensemble (kind, alpha, pole,
+ * beta) and E_g, then thresholds are re-quantised; the chains' lattices, histograms and
+ * round-trip records stay.  Serves the profile scan: a density of states estimated once per
+ * realization (Sec. II: determined once, then shared by the ensembles compared) is copied to
+ * chains of the same realization that then build other ensembles (muca_build_ensemble).
+ * Host int32 lists; pairs must share L and b_top; a chain may not be a destination twice nor
+ * both a source and a destination (EA_EINVAL). */
+int muca_copy_weights(ea_ctx *ctx, const int32_t *src, const int32_t *dst, int n);
+
 /* a4 for the listed chains only (host int32 chain indices); see muca_update_weights. */
 int muca_update_weights_subset(ea_ctx *ctx, const int32_t *chains, int n);
 

@@ -832,6 +832,66 @@ extern "C" int muca_update_weights_subset(ea_ctx *ctx, const int32_t *chains, in
     return EA_OK;
 }
 
+// dst chain k takes src chain k's ln W row, ensemble (kind and parameters) and E_g
+__global__ void copy_weights_kernel(SlotState *__restrict__ slots, double *__restrict__ lnW,
+                                    const int32_t *__restrict__ meta, const uint64_t *__restrict__ off, int n) {
+    const int k = blockIdx.x;
+    if (k >= n) return;
+    const int ss_src = meta[4 * k + 0], ss_dst = meta[4 * k + 1], len = meta[4 * k + 2];
+    const double *w_src = lnW + off[2 * k + 0];
+    double *w_dst = lnW + off[2 * k + 1];
+    for (int b = threadIdx.x; b < len; b += blockDim.x) w_dst[b] = w_src[b];
+    if (threadIdx.x == 0) {
+        const SlotState a = slots[ss_src];
+        SlotState &d = slots[ss_dst];
+        d.kind = a.kind;
+        d.alpha = a.alpha;
+        d.pole = a.pole;
+        d.beta = a.beta;
+        d.e_g = a.e_g;
+        d.b_g = a.b_g;
+    }
+}
+
+extern "C" int muca_copy_weights(ea_ctx *ctx, const int32_t *src, const int32_t *dst, int n) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (n < 0 || (n > 0 && (!src || !dst))) return fail(EA_EINVAL, "bad chain lists");
+    if (n == 0) return EA_OK;
+    const int nc = (int)ctx->chain_slot.size();
+    std::vector<int32_t> meta(4 * (size_t)n);
+    std::vector<uint64_t> off(2 * (size_t)n);
+    std::vector<char> seen(nc, 0);
+    for (int k = 0; k < n; ++k) {
+        const int a = src[k], b = dst[k];
+        if (a < 0 || a >= nc || b < 0 || b >= nc) return fail(EA_EINVAL, "chain index out of range");
+        if (seen[b]) return fail(EA_EINVAL, "chain %d is a destination twice", b);
+        seen[b] = 1;
+        const TileDesc &ta = ctx->tiles[ctx->chain_slot[a] / kTile], &tb = ctx->tiles[ctx->chain_slot[b] / kTile];
+        if (ta.L != tb.L || ctx->chain_btop[a] != ctx->chain_btop[b])
+            return fail(EA_EINVAL, "chains %d and %d differ in L or in their energy range", a, b);
+        meta[4 * k + 0] = ctx->chain_slot[a];
+        meta[4 * k + 1] = ctx->chain_slot[b];
+        meta[4 * k + 2] = ctx->chain_btop[a] + 1;
+        off[2 * k + 0] = ctx->chain_woff[a];
+        off[2 * k + 1] = ctx->chain_woff[b];
+    }
+    for (int k = 0; k < n; ++k)
+        if (seen[src[k]]) return fail(EA_EINVAL, "chain %d is both a source and a destination", src[k]);
+    void *scr;
+    int rc = ctx_scratch(ctx, meta.size() * 4 + off.size() * 8 + 512, &scr);
+    if (rc) return rc;
+    uint64_t *d_off = (uint64_t *)scr;
+    int32_t *d_meta = (int32_t *)((char *)scr + ((off.size() * 8 + 255) & ~(size_t)255));
+    EA_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    EA_CUDA(cudaMemcpyAsync(d_meta, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    copy_weights_kernel<<<n, 128, 0, ctx->stream>>>(ctx->d_slots, ctx->d_lnW, d_meta, d_off, n);
+    EA_CUDA(cudaGetLastError());
+    EA_CUDA(launch_quantize(ctx->d_tiles, (int)ctx->tiles.size(), ctx->d_slots, ctx->d_lnW, ctx->d_thr,
+                            ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
 extern "C" int get_roundtrips(ea_ctx *ctx, int chain0, int n, ea_rt_stats *out, int reset) {
     int rc = ctx_check_range(ctx, chain0, n);
     if (rc || n == 0) return rc;

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ea_reset_chains": (_i, [P, P, _i, P, P]),
     "muca_set_sweep_multiplier": (_i, [P, _i, _i]),
     "muca_update_weights_subset": (_i, [P, P, _i]),
+    "muca_copy_weights": (_i, [P, P, P, _i]),
     "ea_graph_capture": (_i, [P, _i, _u64, _i, _i]),
     "ea_graph_launch": (_i, [P, _i]),
     "ea_graph_release": (_i, [P]),
@@ -279,6 +280,12 @@ class Context:
 
     def set_sweep_multiplier(self, L: int, multiplier: int):
         check(lib().muca_set_sweep_multiplier(self._h, L, multiplier))
+
+    def copy_weights(self, src, dst):
+        a = np.ascontiguousarray(src, dtype=np.int32)
+        b = np.ascontiguousarray(dst, dtype=np.int32)
+        assert a.shape == b.shape
+        check(lib().muca_copy_weights(self._h, _p(a), _p(b), a.shape[0]))
 
     def update_weights_subset(self, chains):
         c = np.ascontiguousarray(chains, dtype=np.int32)

@@ -1,0 +1,111 @@
+"""Profile-parameter scan of the power-law ensemble (Sec. II, Eq. "power_law"), batched.
+
+The paper tunes the two profile parameters (exponent alpha, pole offset Delta E) by comparing
+mean round-trip times (Sec. III) over its disorder realizations, with the density of states of
+each realization determined once and shared by the ensembles compared.  Here every step runs
+on the device in one context:
+
+1. density of states: one flat chain per realization iterates its weights (Sec. II recursion,
+   plain or Berg's accumulated form); ln Omega = -ln W afterwards, E_g = its lowest energy;
+2. for each parameter pair (alpha, Delta E), one chain per realization (a separate random
+   stream) receives that estimate (muca_copy_weights) and builds its power-law weights
+   (muca_build_ensemble); one more set builds the 1/k ensemble (Eq. "1/k");
+3. production: all chains -- the flat ones included -- sweep in one batched launch with
+   round-trip counting; tau_i = (t_last - t_first) / n_rt per chain.
+
+The result holds, per ensemble, the per-realization round-trip times, their mean, the number
+of realizations without a round trip, and (Sec. III) the ratio of mean round-trip times to the
+flat ensemble with a jackknife error over realizations that have a round trip in both.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import analysis, eamc
+
+
+@dataclass
+class ScanResult:
+    labels: list            # ensemble names, "flat", "1/k", "pl(alpha,dE)"
+    params: list            # (kind, alpha, pole) per label
+    tau: np.ndarray         # [ensembles, realizations] round-trip time in sweeps (inf: none)
+    n_rt: np.ndarray        # [ensembles, realizations]
+    requeue: np.ndarray     # [ensembles, realizations] a lower energy than E_g was found
+    e_g: np.ndarray         # [realizations] E_g from the density-of-states stage
+
+    def summary(self) -> list[dict]:
+        out = []
+        flat = self.tau[0]
+        for k, lab in enumerate(self.labels):
+            t = self.tau[k]
+            ok = np.isfinite(t)
+            rec = {"ensemble": lab, "mean_tau": float(np.mean(t[ok])) if ok.any() else math.inf,
+                   "median_tau": float(np.median(t[ok])) if ok.any() else math.inf,
+                   "without_rt": int((~ok).sum()), "requeued": int(self.requeue[k].sum())}
+            both = ok & np.isfinite(flat)
+            if k > 0 and both.sum() >= 3:
+                r, err = analysis.jackknife(t[both], flat[both], np.mean)
+                rec["tau_over_flat"], rec["tau_over_flat_err"] = float(r), float(err)
+            out.append(rec)
+        return out
+
+    def best(self) -> dict:
+        rows = [r for r in self.summary() if r["ensemble"].startswith("pl")]
+        return min(rows, key=lambda r: r.get("tau_over_flat", math.inf))
+
+
+def profile_scan(dim: int, L: int, n_real: int, alphas, poles, seed: int = 0, rid0: int = 0,
+                 dos_iters: int = 30, dos_sweeps: int = 2000, recursion: int = eamc.EA_REC_BERG,
+                 prod_sweeps: int = 20000, with_one_over_k: bool = True, stream=None) -> ScanResult:
+    """Runs the three stages above for every (alpha, Delta E) in alphas x poles."""
+    ctx = eamc.Context(seed=seed, stream=stream)
+    try:
+        # 1. density of states (flat chains, stream 0)
+        dos = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=0)
+        ctx.set_ensemble(dos, n_real, eamc.EA_FLAT)
+        ctx.set_recursion(dos, n_real, recursion)
+        for _ in range(dos_iters):
+            ctx.run_sweeps(dos_sweeps)
+            ctx.update_weights()
+        ctx.set_eg(dos, n_real, None)
+        # 2. one chain per realization and ensemble, each on its own random stream
+        grid = [(a, p) for a in alphas for p in poles]
+        labels, params, firsts = ["flat"], [(eamc.EA_FLAT, 0.0, 0.0)], [dos]
+        for j, (a, p) in enumerate(grid):
+            first = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=1 + j)
+            labels.append(f"pl({a:g},{p:g})")
+            params.append((eamc.EA_POWERLAW, a, p))
+            firsts.append(first)
+        if with_one_over_k:
+            first = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=1 + len(grid))
+            labels.append("1/k")
+            params.append((eamc.EA_ONE_OVER_K, 0.0, 0.0))
+            firsts.append(first)
+        src = np.concatenate([np.arange(dos, dos + n_real)] * (len(firsts) - 1)).astype(np.int32)
+        dst = np.concatenate([np.arange(f, f + n_real) for f in firsts[1:]]).astype(np.int32)
+        ctx.copy_weights(src, dst)
+        for (kind, a, p), f in zip(params[1:], firsts[1:]):
+            ctx.build_ensemble(f, n_real, kind, alpha=a, pole=p if p > 0 else 96.0)
+        # the production chains start their clocks now
+        ctx.roundtrips(reset=True)
+        # 3. production
+        ctx.run_sweeps(prod_sweeps, count_roundtrips=True)
+        R = ctx.roundtrips()
+        E = len(firsts)
+        tau = np.full((E, n_real), math.inf)
+        nrt = np.zeros((E, n_real), dtype=np.int64)
+        req = np.zeros((E, n_real), dtype=bool)
+        for k, f in enumerate(firsts):
+            for r in range(n_real):
+                rec = R[f + r]
+                nrt[k, r] = rec["n_rt"]
+                req[k, r] = bool(rec["requeue"])
+                if rec["n_rt"] > 0:
+                    tau[k, r] = (rec["t_last"] - rec["t_first"]) / rec["n_rt"]
+        e_g = np.array([R[dos + r]["e_g"] for r in range(n_real)])
+        return ScanResult(labels, params, tau, nrt, req, e_g)
+    finally:
+        ctx.close()
