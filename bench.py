@@ -475,10 +475,10 @@ def bench_recursion(L: int = 8, n: int = 256, iters: int = 24, S: int = 2000, P:
     return out
 
 
-def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 30, dos_sweeps: int = 2000,
+def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 40, dos_sweeps: int = 4000,
                        prod_sweeps: int = 20000):
     """Profile-parameter scan (Sec. II): power-law alpha x Delta E grid, flat and 1/k beside
-    it, n_real realizations of L^3, density of states once per realization (flat chains,
+    it, n_real realizations of L^3, density of states once per realization (power-law target,
     Berg's recursion), production with round-trip counting in one batched launch.  Reports the
     mean round-trip time per ensemble and its ratio to flat (jackknife over realizations)."""
     import time

@@ -5,13 +5,14 @@ mean round-trip times (Sec. III) over its disorder realizations, with the densit
 each realization determined once and shared by the ensembles compared.  Here every step runs
 on the device in one context:
 
-1. density of states: one flat chain per realization iterates its weights (Sec. II recursion,
-   plain or Berg's accumulated form); ln Omega = -ln W afterwards, E_g = its lowest energy;
-2. for each parameter pair (alpha, Delta E), one chain per realization (a separate random
-   stream) receives that estimate (muca_copy_weights) and builds its power-law weights
-   (muca_build_ensemble); one more set builds the 1/k ensemble (Eq. "1/k");
-3. production: all chains -- the flat ones included -- sweep in one batched launch with
-   round-trip counting; tau_i = (t_last - t_first) / n_rt per chain.
+1. density of states: one chain per realization iterates its weights with a power-law target
+   (as the paper determined its densities of states; Sec. II recursion, plain or Berg's
+   accumulated form); ln Omega = ln P_SH - ln W afterwards, E_g = its lowest energy;
+2. for the flat ensemble, each parameter pair (alpha, Delta E) and the 1/k ensemble
+   (Eq. "1/k"), one chain per realization (a separate random stream) receives that estimate
+   (muca_copy_weights) and builds its weights (muca_build_ensemble);
+3. production: all chains sweep in one batched launch with round-trip counting;
+   tau_i = (t_last - t_first) / n_rt per chain (the estimation chains sweep along, unused).
 
 The result holds, per ensemble, the per-realization round-trip times, their mean, the number
 of realizations without a round trip, and (Sec. III) the ratio of mean round-trip times to the
@@ -59,36 +60,32 @@ class ScanResult:
 
 def profile_scan(dim: int, L: int, n_real: int, alphas, poles, seed: int = 0, rid0: int = 0,
                  dos_iters: int = 30, dos_sweeps: int = 2000, recursion: int = eamc.EA_REC_BERG,
-                 prod_sweeps: int = 20000, with_one_over_k: bool = True, stream=None) -> ScanResult:
+                 dos_alpha: float = -3.6, dos_pole: float = 96.0, prod_sweeps: int = 20000,
+                 with_one_over_k: bool = True, stream=None) -> ScanResult:
     """Runs the three stages above for every (alpha, Delta E) in alphas x poles."""
     ctx = eamc.Context(seed=seed, stream=stream)
     try:
-        # 1. density of states (flat chains, stream 0)
+        # 1. density of states (power-law target, stream 0)
         dos = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=0)
-        ctx.set_ensemble(dos, n_real, eamc.EA_FLAT)
+        ctx.set_ensemble(dos, n_real, eamc.EA_POWERLAW, dos_alpha, dos_pole)
         ctx.set_recursion(dos, n_real, recursion)
         for _ in range(dos_iters):
             ctx.run_sweeps(dos_sweeps)
             ctx.update_weights()
         ctx.set_eg(dos, n_real, None)
         # 2. one chain per realization and ensemble, each on its own random stream
-        grid = [(a, p) for a in alphas for p in poles]
-        labels, params, firsts = ["flat"], [(eamc.EA_FLAT, 0.0, 0.0)], [dos]
-        for j, (a, p) in enumerate(grid):
-            first = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=1 + j)
-            labels.append(f"pl({a:g},{p:g})")
-            params.append((eamc.EA_POWERLAW, a, p))
-            firsts.append(first)
+        params = [(eamc.EA_FLAT, 0.0, 0.0)] + [(eamc.EA_POWERLAW, a, p) for a in alphas for p in poles]
+        labels = ["flat"] + [f"pl({a:g},{p:g})" for _, a, p in params[1:]]
         if with_one_over_k:
-            first = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=1 + len(grid))
-            labels.append("1/k")
             params.append((eamc.EA_ONE_OVER_K, 0.0, 0.0))
-            firsts.append(first)
-        src = np.concatenate([np.arange(dos, dos + n_real)] * (len(firsts) - 1)).astype(np.int32)
-        dst = np.concatenate([np.arange(f, f + n_real) for f in firsts[1:]]).astype(np.int32)
+            labels.append("1/k")
+        firsts = [ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=1 + j) for j in range(len(params))]
+        src = np.concatenate([np.arange(dos, dos + n_real)] * len(firsts)).astype(np.int32)
+        dst = np.concatenate([np.arange(f, f + n_real) for f in firsts]).astype(np.int32)
         ctx.copy_weights(src, dst)
-        for (kind, a, p), f in zip(params[1:], firsts[1:]):
-            ctx.build_ensemble(f, n_real, kind, alpha=a, pole=p if p > 0 else 96.0)
+        for (kind, a, p), f in zip(params, firsts):
+            ctx.build_ensemble(f, n_real, kind, alpha=a if kind == eamc.EA_POWERLAW else dos_alpha,
+                               pole=p if kind == eamc.EA_POWERLAW else dos_pole)
         # the production chains start their clocks now
         ctx.roundtrips(reset=True)
         # 3. production

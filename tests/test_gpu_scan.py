@@ -53,16 +53,18 @@ def test_profile_scan_matches_oracle(eamc, orc):
         for _ in range(iters):
             dos.hist[:] = 0
             dos.sweeps(S, orc.quantize(dim, lnW))
-            lnW = orc.update_weights_berg(dim, L, dos.parity, 0, 0.0, 1.0, dos.rt.e_min, lnW,
+            lnW = orc.update_weights_berg(dim, L, dos.parity, 1, -3.6, 96.0, dos.rt.e_min, lnW,
                                           dos.hist, acc)
         e_g = int(dos.rt.e_min)
         assert res.e_g[r] == e_g
+        lnP = np.array([orc.ln_profile(1, -3.6, 96.0, e_g, orc.energy_of_bin(dim, L, dos.parity, b))
+                        for b in range(dos.b_top + 1)])
+        lnO = lnP - lnW
         for k, (kind, a, p) in enumerate(res.params):
-            if k == 0:
-                ch, w = dos, lnW
-            else:
-                ch = orc.Chain(dim, L, seed, r, stream=k)
-                w = orc.build_weights(dim, L, ch.parity, kind, a, p if p > 0 else 96.0, 1.0, e_g, -lnW)
+            ch = orc.Chain(dim, L, seed, r, stream=1 + k)
+            if kind != 1:
+                a, p = -3.6, 96.0
+            w = orc.build_weights(dim, L, ch.parity, kind, a, p, 1.0, e_g, lnO)
             ch.rt = orc.RT(phase=0, n_rt=0, t_first=-1, t_last=-1, e_min=ch.E, e_g=e_g, requeue=0, pad=0)
             ch.sweeps(P, orc.quantize(dim, w), count_rt=True)
             assert res.n_rt[k, r] == ch.rt.n_rt, (k, r)
