@@ -31,7 +31,7 @@ namespace eamc {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr int kWarps = 4;                 // consumer, bond sums, two random-number warps
+constexpr int kWarps = 4;                 // consumer, bond sums + measurement, two random-number warps
 constexpr int kThreads = 32 * kWarps;
 
 template <int L>
@@ -68,14 +68,19 @@ struct Geo {
     static constexpr int V = NR * L;
     static constexpr int B = ((DIM * V) / 2 >> 1) + 1;       // table rows per chain
     static constexpr int NG = (L + 3) / 4;                   // Philox calls per row
-    static constexpr int FIELDS = DIM + 2;                   // S, Jx, Jx(shifted), Jy, (Jz)
+    static constexpr int FIELDS = DIM + 1;                   // S, Jx, Jy, (Jz)
     static constexpr int SUMQ = sizeof(T) == 4 ? 1 : 2;      // uint4 slots for sA,sB,R,JYm
     static constexpr int HQ = SUMQ + NG;                     // uint4 slots per lane per row
+    static constexpr int LAG = (L >= 4 && L <= 8) ? 2 : 1;  // rows the producers run ahead
+    static constexpr int NBUF = LAG + 1;                      // records in the ring
     static constexpr size_t LATTICE_BYTES = (size_t)FIELDS * NR * 32 * sizeof(T);
-    static constexpr size_t HAND_BYTES = (size_t)2 * HQ * 32 * 16;
+    static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * 32 * 16;
+    static constexpr size_t RES_BYTES = (size_t)2 * L * 32 * sizeof(int);  // row offsets for warp 4
     static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * 32 * sizeof(uint32_t);
-    static constexpr bool SMEM_THR = LATTICE_BYTES + HAND_BYTES + THR_BYTES <= 200 * 1024;
-    static constexpr size_t SMEM = LATTICE_BYTES + HAND_BYTES + (SMEM_THR ? THR_BYTES : 0);
+    static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES;
+    // up to 225 KB of the 227 KB a block may use (the rest: static shared memory)
+    static constexpr bool SMEM_THR = BASE_BYTES + THR_BYTES <= 225 * 1024;
+    static constexpr size_t SMEM = BASE_BYTES + (SMEM_THR ? THR_BYTES : 0);
 };
 
 template <bool SMEM>
@@ -106,12 +111,17 @@ __device__ __forceinline__ void get4(const uint4 *slots, int q, int lane, T &a, 
     }
 }
 
-// Four warps per tile.  Warps 1..3 (producers) work one row ahead of warp 0 (consumer): warp
-// 1 sums, per site, the unsatisfied-bond indicators of the bonds that cannot change while the
-// consumer sweeps that row; warps 2 and 3 draw the row's random words (Philox calls g = 2, 3
-// mod 2).  The consumer adds the bond to the row it has just finished (-y) and runs the
-// sequential accept / reject chain.  A block barrier per row hands over a double-buffered
-// record.
+// Four warps per tile.  Warp 0 (consumer) runs the sequential accept / reject chain of the 32
+// chains.  Warps 1..3 (producers) work LAG rows ahead of it: warp 1 sums, per site, the
+// unsatisfied-bond indicators of the bonds that cannot change while the consumer sweeps that
+// row; warps 2 and 3 draw the row's random words (Philox call g of the row from warp 2 + g % 2).
+// Warp 1 also measures, one row behind the consumer: from the row offsets the consumer leaves
+// after each attempt it keeps the lowest energy, the round-trip state and the histogram.  One
+// block barrier per row; records live in a ring of LAG + 1 buffers, results in two.
+//
+// Running LAG rows ahead is exact as long as every row a record reads as final has been swept:
+// besides the -y row (which the consumer adds itself), the last row of a plane (y = L-1) reads
+// the plane's first row, L-1 rows back, so LAG <= L-2; the -z row is L rows back.
 template <int DIM, int L>
 __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotState *__restrict__ slots,
                                            uint32_t *__restrict__ spins,
@@ -121,21 +131,20 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
                                            PhiloxKey key, int count_rt, unsigned char *smem_raw) {
     using G = Geo<DIM, L>;
     using T = typename G::T;
-    constexpr int NR = G::NR;
+    constexpr int NR = G::NR, LAG = G::LAG, NBUF = G::NBUF;
     constexpr T NIB = nib_mask<T, L>();
     constexpr T LASTNIB = T(1) << (4 * (L - 1));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool producer = warp >= 1;
 
     // ---- stage the lattice as nibble-packed row words, lane-interleaved: word k of lane l
     //      at [k*32 + l].  Nibble x of a row word is site x of that row.
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *Rs = sm;                  // spins, nibble = 1 if S = -1
     T *JXs = sm + NR * 32;       // bond (x, x+1) has J = -1
-    T *JXms = sm + 2 * NR * 32;  // bond (x-1, x) has J = -1
-    T *JYs = sm + 3 * NR * 32;   // bond (x,y)-(x,y+1)
-    T *JZs = sm + 4 * NR * 32;   // bond (x,y,z)-(x,y,z+1)   (DIM == 3)
+    T *JYs = sm + 2 * NR * 32;   // bond (x,y)-(x,y+1)
+    T *JZs = sm + 3 * NR * 32;   // bond (x,y,z)-(x,y,z+1)   (DIM == 3)
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
+    int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2][L][32]
     const uint32_t *gsp = spins + td.spin_off;
     const uint32_t *gbd = bonds + td.bond_off;
     for (int row = warp; row < NR; row += kWarps) {
@@ -150,7 +159,6 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         }
         Rs[row * 32 + lane] = r;
         JXs[row * 32 + lane] = jx;
-        JXms[row * 32 + lane] = rot_prev<T, L>(jx);
         JYs[row * 32 + lane] = jy;
         if constexpr (DIM == 3) JZs[row * 32 + lane] = jz;
     }
@@ -166,7 +174,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     constexpr int RSB = 8 * NSB;
     const char *tab;
     if constexpr (G::SMEM_THR) {
-        uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);
+        uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES + G::RES_BYTES);
         if (warp == 1) {
             const uint4 *src = reinterpret_cast<const uint4 *>(thr + lrow * 8);
             for (int b = 0; b < G::B; ++b) {
@@ -187,90 +195,158 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     const uint64_t t0 = ss.t;
     const uint64_t total = n_sweeps * (uint64_t)NR;  // rows to sweep
 
-    // producers: record of row `row` (sweep index tt) into buffer `k`
-    auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
-        uint4 *buf = hand + k * G::HQ * 32;
-        if (warp >= 2) {  // random words of the row's sites: Philox call g covers x = 4g .. 4g+3
-            const uint32_t c3 = ss.stream << 8;
-#pragma unroll
-            for (int g = warp - 2; g < G::NG; g += 2)
-                buf[(G::SUMQ + g) * 32 + lane] =
-                    philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
-            return;
-        }
-        const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
-        const T R = Rs[row * 32 + lane];
-        const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * 32 + lane];
-        const T u_xm = R ^ rot_prev<T, L>(R) ^ JXms[row * 32 + lane];
-        T stable = (R ^ Rs[ryp * 32 + lane] ^ JYs[row * 32 + lane]) + (u_xp & ~LASTNIB);
-        if constexpr (DIM == 3) {
-            const int rzm = (z == 0) ? row + (L - 1) * L : row - L;
-            const int rzp = (z == L - 1) ? row - (L - 1) * L : row + L;
-            stable += (R ^ Rs[rzp * 32 + lane] ^ JZs[row * 32 + lane]) +
-                      (R ^ Rs[rzm * 32 + lane] ^ JZs[rzm * 32 + lane]);
-        }
-        // the -y row: the consumer's previous row (add later) unless (3D, y = 0), where it is
-        // the plane's last row, not yet swept
-        T jym = 0;
-        const int rym = (y == 0) ? row + (L - 1) : row - 1;
-        if (DIM == 3 && y == 0) stable += R ^ Rs[rym * 32 + lane] ^ JYs[rym * 32 + lane];
-        else jym = JYs[rym * 32 + lane];
-        const T sA = stable + u_xm;
-        // nibble 0 of sB is never used (site 0 has no dynamic -x bond): its bit 3 carries the
-        // stale wrap bond of site L-1
-        const T wbit = (u_xp >> (4 * (L - 1))) & T(1);
-        const T sB = ((stable + (u_xm ^ NIB)) & ~T(0xF)) | (wbit << 3);
-        put4<T>(buf, 0, lane, sA, sB, R, jym);
-    };
-
     __syncthreads();
-    if (producer) {
-        if (total > 0) produce(0, 0, 0, (uint32_t)t0, 0);
-        int row = 0, y = 0, z = 0;
+    // every warp passes exactly 1 + total + 1 block barriers
+    if (warp >= 1 && warp <= 3) {
+        // ---- producers: record of row `row` (sweep index tt) into ring buffer `k`
+        auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
+            uint4 *buf = hand + k * G::HQ * 32;
+            if (warp >= 2) {  // random words: Philox call g covers sites x = 4g .. 4g+3
+                const uint32_t c3 = ss.stream << 8;
+#pragma unroll
+                for (int g = warp - 2; g < G::NG; g += 2)
+                    buf[(G::SUMQ + g) * 32 + lane] =
+                        philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
+                return;
+            }
+            const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
+            const T R = Rs[row * 32 + lane];
+            const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * 32 + lane];  // bond (x, x+1) at nibble x
+            const T u_xm = rot_prev<T, L>(u_xp);                           // bond (x-1, x) at nibble x
+            T stable = (R ^ Rs[ryp * 32 + lane] ^ JYs[row * 32 + lane]) + (u_xp & ~LASTNIB);
+            if constexpr (DIM == 3) {
+                const int rzm = (z == 0) ? row + (L - 1) * L : row - L;
+                const int rzp = (z == L - 1) ? row - (L - 1) * L : row + L;
+                stable += (R ^ Rs[rzp * 32 + lane] ^ JZs[row * 32 + lane]) +
+                          (R ^ Rs[rzm * 32 + lane] ^ JZs[rzm * 32 + lane]);
+            }
+            // the -y row: the consumer's previous row (added there) unless (3D, y = 0), where
+            // it is the plane's last row, not yet swept
+            T jym = 0;
+            const int rym = (y == 0) ? row + (L - 1) : row - 1;
+            if (DIM == 3 && y == 0) stable += R ^ Rs[rym * 32 + lane] ^ JYs[rym * 32 + lane];
+            else jym = JYs[rym * 32 + lane];
+            const T sA = stable + u_xm;
+            // nibble 0 of sB is never used (site 0 has no dynamic -x bond): its bit 3 carries
+            // the stale wrap bond of site L-1
+            const T wbit = (u_xp >> (4 * (L - 1))) & T(1);
+            const T sB = ((stable + (u_xm ^ NIB)) & ~T(0xF)) | (wbit << 3);
+            put4<T>(buf, 0, lane, sA, sB, R, jym);
+        };
+        int row = 0, y = 0, z = 0, kb = 0;
         uint64_t s = 0;
-        for (uint64_t k = 0; k < total; ++k) {
+        auto advance = [&]() {
             if (++y == L) { y = 0; ++z; }
             if (++row == NR) { row = 0; y = 0; z = 0; ++s; }
-            // barrier k: record k is complete and the consumer has finished with record k-1,
-            // whose buffer ((k+1)&1) is refilled with record k+1
-            __syncthreads();
-            if (k + 1 < total) produce(row, y, z, (uint32_t)(t0 + s), (int)((k + 1) & 1));
+            if (++kb == NBUF) kb = 0;
+        };
+        for (int j = 0; j < LAG && (uint64_t)j < total; ++j) {  // the first LAG records
+            produce(row, y, z, (uint32_t)(t0 + s), kb);
+            advance();
         }
-        return;  // every warp passes exactly 1 + total block barriers
+        // ---- measurement (warp 1), one row behind the consumer: lowest energy, round trips
+        //      (Sec. III) and, after every sweep, H(E) += 1
+        int phase = ss.phase, nrt = ss.n_rt;
+        int64_t tf = ss.t_first, tl = ss.t_last;
+        const int topB = ss.b_top * RSB, botB = ss.b_g * RSB;
+        int pmin = ss.b_min * RSB, pnow = ss.b * RSB;
+        uint32_t *hist_l = hist + lrow;
+        int mrow = 0;
+        uint64_t ms = 0;
+        auto measure = [&](int buf) {
+            const int *r = res + buf * L * 32 + lane;
+            int lo = 0x7FFFFFFF;
+            uint32_t mtop = 0u, mbot = 0u;
+#pragma unroll
+            for (int x = 0; x < L; ++x) {
+                const int pr = r[x * 32];
+                lo = min(lo, pr);
+                mtop |= (uint32_t)(pr >= topB) << x;
+                mbot |= (uint32_t)(pr <= botB) << x;
+                if (x == L - 1) pnow = pr;
+            }
+            pmin = min(pmin, lo);
+            // the attempts of the row in order: a transition at the first attempt that meets
+            // the current phase's condition (E <= E_g heading down, E >= E_top otherwise), the
+            // next one looked for after it
+            if (count_rt && active && ((phase == 1) ? mbot : mtop) != 0u) {
+                const int64_t t = (int64_t)(t0 + ms);
+                int x0 = 0;
+                while (x0 < L) {
+                    const uint32_t m = ((phase == 1) ? mbot : mtop) >> x0;
+                    if (m == 0u) break;
+                    x0 += __ffs(m);  // one past the attempt that meets the condition
+                    if (phase == 0) { tf = t; phase = 1; }
+                    else if (phase == 1) { phase = 2; }
+                    else { nrt += 1; tl = t; phase = 1; }
+                }
+            }
+            if (++mrow == NR) {
+                mrow = 0;
+                ++ms;
+                if (active) atomicAdd(&hist_l[pnow / RSB], 1u);  // no return value: no wait
+            }
+        };
+        for (uint64_t k = 0; k < total; ++k) {
+            // barrier k: records up to k+LAG-1 are complete, the consumer is done with record
+            // k-1 (whose buffer takes record k+LAG) and has left the result of row k-1
+            __syncthreads();
+            if (k + LAG < total) {
+                produce(row, y, z, (uint32_t)(t0 + s), kb);
+                advance();
+            }
+            if (warp == 1 && k > 0) measure((int)((k - 1) & 1));
+        }
+        __syncthreads();
+        if (warp == 1) {
+            if (total > 0) measure((int)((total - 1) & 1));
+            ss.b = pnow / RSB;
+            ss.b_min = pmin / RSB;
+            ss.phase = phase;
+            ss.n_rt = nrt;
+            ss.t_first = tf;
+            ss.t_last = tl;
+            ss.t = t0 + n_sweeps;
+            if (count_rt && active && energy_of_bin(DIM * G::V, ss.parity, ss.b_min) < ss.e_g) ss.requeue = 1;
+            slots[slot] = ss;
+        }
+        return;
     }
 
     // ---- consumer
-    int phase = ss.phase, nrt = ss.n_rt;
-    int64_t tf = ss.t_first, tl = ss.t_last;
-    uint32_t *hist_l = hist + lrow;
-    const int topB = ss.b_top * RSB, botB = ss.b_g * RSB;
-    int pmin = ss.b_min * RSB;
     // the previous attempt, applied lazily: row it was evaluated at (rq), row delta if it was
     // accepted (dq) and whether it was (pa)
     int rq = ss.b * RSB, dq = 0, pa = 0;
-    int pnow = rq;
     T Rprev = Rs[(NR - 1) * 32 + lane];
-    int row = 0, y = 0;
-    uint64_t s = 0;
+    int row = 0, y = 0, kb = 0;
+    // the record of the row to sweep; with LAG >= 2 the next one is complete one barrier early
+    // and is read while the current row runs
+    T nsA, nsB, nR, njym;
+    uint4 nrr[G::NG];
+    auto load_rec = [&](int b) {
+        const uint4 *buf = hand + b * G::HQ * 32;
+        get4<T>(buf, 0, lane, nsA, nsB, nR, njym);
+#pragma unroll
+        for (int g = 0; g < G::NG; ++g) nrr[g] = buf[(G::SUMQ + g) * 32 + lane];
+    };
     for (uint64_t k = 0; k < total; ++k) {
-        __syncthreads();                           // record k is complete
-        const uint4 *buf = hand + (int)(k & 1) * G::HQ * 32;
-        T sA, sB, R, jym;
-        get4<T>(buf, 0, lane, sA, sB, R, jym);
+        __syncthreads();  // barrier k: record k is complete
+        if (LAG == 1 || k == 0) load_rec(kb);
+        T sA = nsA, sB = nsB;
+        const T R = nR, jym = njym;
         uint4 rr[G::NG];
 #pragma unroll
-        for (int g = 0; g < G::NG; ++g) rr[g] = buf[(G::SUMQ + g) * 32 + lane];
+        for (int g = 0; g < G::NG; ++g) rr[g] = nrr[g];
+        if (++kb == NBUF) kb = 0;
+        if (LAG >= 2 && k + 1 < total) load_rec(kb);
         if (DIM == 2 || y > 0) {
             const T uym = R ^ Rprev ^ jym;
             sA += uym;
             sB += uym;
         }
         const int wbit = (int)((sB >> 3) & 1u);
-        T accN = 0;   // nibble x = 1 if this chain flipped site x of the row
-        // measurement after every attempt, off the accept / reject chain: the lowest row
-        // offset of the row and which attempts ended at or above E_top / at or below E_g
-        int lo = 0x7FFFFFFF, plast = 0;
-        uint32_t mtop = 0u, mbot = 0u;
+        T accN = 0;  // nibble x = 1 if this chain flipped site x of the row
+        int *resb = res + (int)(k & 1) * L * 32 + lane;
         // software pipeline: iteration x resolves attempt x from acc(x-1), issues both
         // candidate threshold loads of attempt x+1 (they need only acc(x-1)), then compares
         int nA = (int)(sA & 0xF), nB = nA;
@@ -295,11 +371,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
             const bool acc = active && (th == kAlways || r < th);
             accN |= T(acc ? 1u : 0u) << (4 * x);
-            const int pr = acc ? rx + dx : rx;
-            lo = min(lo, pr);
-            mtop |= (uint32_t)(pr >= topB) << x;
-            mbot |= (uint32_t)(pr <= botB) << x;
-            plast = pr;
+            resb[x * 32] = acc ? rx + dx : rx;  // row offset after the attempt, for warp 4
             rq = rx;
             dq = dx;
             pa = acc ? 1 : 0;
@@ -307,33 +379,13 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         const T Rfin = R ^ accN;
         Rs[row * 32 + lane] = Rfin;
         Rprev = Rfin;
-        pmin = min(pmin, lo);
-        pnow = plast;
-        // round trips (Sec. III): the attempts of this row in order; a transition happens at
-        // the first attempt that meets the current phase's condition (E <= E_g heading down,
-        // E >= E_top otherwise), the next one is looked for after it (rare: a few rows a sweep)
-        if (count_rt && active && ((phase == 1) ? mbot : mtop) != 0u) {
-            const int64_t t = (int64_t)(t0 + s);
-            int x0 = 0;
-            while (x0 < L) {
-                const uint32_t m = ((phase == 1) ? mbot : mtop) >> x0;
-                if (m == 0u) break;
-                x0 += __ffs(m);  // one past the attempt that meets the condition
-                if (phase == 0) { tf = t; phase = 1; }
-                else if (phase == 1) { phase = 2; }
-                else { nrt += 1; tl = t; phase = 1; }
-            }
-        }
         if (++y == L) y = 0;
         if (++row == NR) {
             row = 0;
             y = 0;
-            ++s;
-            if (active) atomicAdd(&hist_l[pnow / RSB], 1u);  // no return value: no wait
         }
     }
-    __syncwarp();
-    const int bnow = pnow / RSB, bmin = pmin / RSB;
+    __syncthreads();
     // spins back to the multi-spin-coded global layout
     for (int r2 = 0; r2 < NR; ++r2) {
         const T Rw = Rs[r2 * 32 + lane];
@@ -343,18 +395,9 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             if (lane == 0) spins[td.spin_off + r2 * L + x] = m;
         }
     }
-    ss.b = bnow;
-    ss.b_min = bmin;
-    ss.phase = phase;
-    ss.n_rt = nrt;
-    ss.t_first = tf;
-    ss.t_last = tl;
-    ss.t = t0 + n_sweeps;
-    if (count_rt && active && energy_of_bin(DIM * G::V, ss.parity, bmin) < ss.e_g) ss.requeue = 1;
-    slots[slot] = ss;
 }
 
-// Four warps (consumer + producers) per tile of 32 chains; the tile's L selects the body.
+// Four warps per tile of 32 chains; the tile's L selects the body.
 // Direct mode (queue == nullptr): block b sweeps tile tile_list[b] (or b).  Persistent mode:
 // a grid sized to the resident capacity pulls positions of tile_list (longest tiles first)
 // from the counter *queue until n_work positions are taken.
