@@ -31,7 +31,13 @@ namespace eamc {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr int kWarps = 4;                 // consumer, bond sums + measurement, two random-number warps
+// warps: 0 consumer, 1 bond sums, 2-3 random numbers, kMeasureWarp measurement (warp 1 as well
+// when the block has four warps)
+#ifndef EAMC_SWEEP_WARPS
+#define EAMC_SWEEP_WARPS 4
+#endif
+constexpr int kWarps = EAMC_SWEEP_WARPS;
+constexpr int kMeasureWarp = kWarps == 5 ? 4 : 1;
 constexpr int kThreads = 32 * kWarps;
 
 template <int L>
@@ -197,7 +203,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
 
     __syncthreads();
     // every warp passes exactly 1 + total + 1 block barriers
-    if (warp >= 1 && warp <= 3) {
+    if (warp >= 1) {
         // ---- producers: record of row `row` (sweep index tt) into ring buffer `k`
         auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
             uint4 *buf = hand + k * G::HQ * 32;
@@ -240,11 +246,12 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             if (++row == NR) { row = 0; y = 0; z = 0; ++s; }
             if (++kb == NBUF) kb = 0;
         };
-        for (int j = 0; j < LAG && (uint64_t)j < total; ++j) {  // the first LAG records
+        const bool producer = warp <= 3;
+        for (int j = 0; producer && j < LAG && (uint64_t)j < total; ++j) {  // the first LAG records
             produce(row, y, z, (uint32_t)(t0 + s), kb);
             advance();
         }
-        // ---- measurement (warp 1), one row behind the consumer: lowest energy, round trips
+        // ---- measurement (warp kMeasureWarp), one row behind the consumer: lowest energy, round trips
         //      (Sec. III) and, after every sweep, H(E) += 1
         int phase = ss.phase, nrt = ss.n_rt;
         int64_t tf = ss.t_first, tl = ss.t_last;
@@ -291,14 +298,14 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             // barrier k: records up to k+LAG-1 are complete, the consumer is done with record
             // k-1 (whose buffer takes record k+LAG) and has left the result of row k-1
             __syncthreads();
-            if (k + LAG < total) {
+            if (producer && k + LAG < total) {
                 produce(row, y, z, (uint32_t)(t0 + s), kb);
                 advance();
             }
-            if (warp == 1 && k > 0) measure((int)((k - 1) & 1));
+            if (warp == kMeasureWarp && k > 0) measure((int)((k - 1) & 1));
         }
         __syncthreads();
-        if (warp == 1) {
+        if (warp == kMeasureWarp) {
             if (total > 0) measure((int)((total - 1) & 1));
             ss.b = pnow / RSB;
             ss.b_min = pmin / RSB;
