@@ -31,13 +31,19 @@ namespace eamc {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-// warps: 0 consumer, 1 bond sums, 2-3 random numbers, kMeasureWarp measurement (warp 1 as well
-// when the block has four warps)
+// warps: 0 consumer, 1 bond sums, 2-3 random numbers, kMeasureWarp measurement.  Warp w issues
+// on scheduler w % 4: with six warps the measurement (warp 5) shares the bond-sum warp's
+// scheduler and warp 4 only takes part in the barriers, so nothing competes with the consumer
+// for its scheduler (five warps, measurement on warp 4 beside the consumer, and four, the
+// bond-sum warp measuring as well, were both measured slower on the L = 6 batch).
 #ifndef EAMC_SWEEP_WARPS
-#define EAMC_SWEEP_WARPS 4
+#define EAMC_SWEEP_WARPS 6
 #endif
 constexpr int kWarps = EAMC_SWEEP_WARPS;
-constexpr int kMeasureWarp = kWarps == 5 ? 4 : 1;
+#ifndef EAMC_MEASURE_WARP
+#define EAMC_MEASURE_WARP (EAMC_SWEEP_WARPS >= 5 ? EAMC_SWEEP_WARPS - 1 : 1)
+#endif
+constexpr int kMeasureWarp = EAMC_MEASURE_WARP;
 constexpr int kThreads = 32 * kWarps;
 
 template <int L>
@@ -117,13 +123,15 @@ __device__ __forceinline__ void get4(const uint4 *slots, int q, int lane, T &a, 
     }
 }
 
-// Four warps per tile.  Warp 0 (consumer) runs the sequential accept / reject chain of the 32
+// kWarps warps per tile.  Warp 0 (consumer) runs the sequential accept / reject chain of the 32
 // chains.  Warps 1..3 (producers) work LAG rows ahead of it: warp 1 sums, per site, the
 // unsatisfied-bond indicators of the bonds that cannot change while the consumer sweeps that
 // row; warps 2 and 3 draw the row's random words (Philox call g of the row from warp 2 + g % 2).
-// Warp 1 also measures, one row behind the consumer: from the row offsets the consumer leaves
-// after each attempt it keeps the lowest energy, the round-trip state and the histogram.  One
-// block barrier per row; records live in a ring of LAG + 1 buffers, results in two.
+// Warp kMeasureWarp measures, one row behind the consumer: from the row offsets the consumer
+// leaves after each attempt it keeps the lowest energy, the round-trip state and the histogram.
+// One block barrier per row; records live in a ring of LAG + 1 buffers, results in two.  At the
+// end of a row the consumer already loads the candidate thresholds of the next row's first
+// attempt (the next record is in its registers), so a row starts with a decision.
 //
 // Running LAG rows ahead is exact as long as every row a record reads as final has been swept:
 // besides the -y row (which the consumer adds itself), the last row of a plane (y = L-1) reads
@@ -336,6 +344,10 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
 #pragma unroll
         for (int g = 0; g < G::NG; ++g) nrr[g] = buf[(G::SUMQ + g) * 32 + lane];
     };
+    // candidate thresholds of the next attempt; with LAG >= 2 the last attempt of a row already
+    // loads those of the next row's first attempt (its record is in registers by then)
+    uint32_t thA = 0u, thB = 0u;
+    bool have_next = false;
     for (uint64_t k = 0; k < total; ++k) {
         __syncthreads();  // barrier k: record k is complete
         if (LAG == 1 || k == 0) load_rec(kb);
@@ -357,8 +369,14 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         // software pipeline: iteration x resolves attempt x from acc(x-1), issues both
         // candidate threshold loads of attempt x+1 (they need only acc(x-1)), then compares
         int nA = (int)(sA & 0xF), nB = nA;
-        uint32_t thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + nA * NSB));
-        uint32_t thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + dq + nB * NSB));
+        if (!have_next) {
+            thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + nA * NSB));
+            thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rq + dq + nB * NSB));
+        }
+        have_next = false;
+        // does the next row add its -y bond (the row just finished) itself?
+        const int y_next = (y + 1 == L || row + 1 == NR) ? 0 : y + 1;
+        const bool next_uym = (DIM == 2 || y_next > 0);
 #pragma unroll
         for (int x = 0; x < L; ++x) {
             const uint32_t th = pa ? thB : thA;
@@ -374,11 +392,20 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
                 }
                 thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + nA * NSB));
                 thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + dx + nB * NSB));
+            } else if (LAG >= 2 && k + 1 < total) {
+                // first attempt of the next row: its class needs that row's record and, through
+                // the -y bond, only site 0 of this row (final since attempt 0); both candidate
+                // bins depend on this attempt
+                const T rfin0 = (R ^ accN) & T(1);
+                const int n0 = (int)(nsA & 0xF) + (next_uym ? (int)((nR ^ rfin0 ^ njym) & T(1)) : 0);
+                thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + n0 * NSB));
+                thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + dx + n0 * NSB));
+                have_next = true;
             }
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
             const bool acc = active && (th == kAlways || r < th);
             accN |= T(acc ? 1u : 0u) << (4 * x);
-            resb[x * 32] = acc ? rx + dx : rx;  // row offset after the attempt, for warp 4
+            resb[x * 32] = acc ? rx + dx : rx;  // row offset after the attempt, for the measurement
             rq = rx;
             dq = dx;
             pa = acc ? 1 : 0;
@@ -404,7 +431,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     }
 }
 
-// Four warps per tile of 32 chains; the tile's L selects the body.
+// kWarps warps per tile of 32 chains; the tile's L selects the body.
 // Direct mode (queue == nullptr): block b sweeps tile tile_list[b] (or b).  Persistent mode:
 // a grid sized to the resident capacity pulls positions of tile_list (longest tiles first)
 // from the counter *queue until n_work positions are taken.
