@@ -382,6 +382,39 @@ def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 4000):
             "adapted_spread_from_counting_noise_alone": noise_spread}
 
 
+def uneven_groups():
+    """(kind index, L, first realization id, count) of the uneven batch: realization ids with
+    L = Ls[id % 5], one contiguous id block per L; kind 0 power law, 1 flat, 2 1/k."""
+    from paper_2011_08560_gb300.workloads import UNEVEN
+    Ls = UNEVEN["Ls"]
+    out = []
+    for kind_idx in range(3):
+        for L in Ls:
+            n = sum(1 for r in range(UNEVEN["n_real"]) if Ls[r % len(Ls)] == L)
+            out.append((kind_idx, L, Ls.index(L) * UNEVEN["n_real"], n))
+    return out
+
+
+def build_uneven(eamc, autotune, stream_ptr, S: int):
+    """The uneven batch as the bench runs it: chains, autotuned launch, one iteration step, then
+    the 1/k chains take 1/k weights built from their estimate."""
+    from paper_2011_08560_gb300.workloads import UNEVEN
+    ctx = eamc.Context(seed=UNEVEN["seed"], device=0, stream=stream_ptr)
+    groups, one_over_k = [], []
+    for kind_idx, L, rid0, n in uneven_groups():
+        first = ctx.init_disorder(3, L, n, rid0=rid0, stream=kind_idx)
+        ctx.set_ensemble(first, n, eamc.EA_POWERLAW if kind_idx == 0 else eamc.EA_FLAT)
+        if kind_idx == 2:
+            one_over_k.append((first, n))
+        groups.append((3, L, n))
+    best = autotune.apply(ctx, groups, sweeps=20)
+    ctx.run_sweeps(S, count_roundtrips=False)
+    ctx.update_weights()
+    for first, n in one_over_k:
+        ctx.build_ensemble(first, n, eamc.EA_ONE_OVER_K)
+    return ctx, groups, best
+
+
 def bench_uneven(S: int = 100, iters: int = 3):
     """Uneven batch: 4096 realizations, L uniform over {4,6,8,10,12} (round robin by id), each
     as a power-law, a flat and a 1/k chain, in one persistent launch per step; the
@@ -389,26 +422,8 @@ def bench_uneven(S: int = 100, iters: int = 3):
     import torch
 
     from paper_2011_08560_gb300 import autotune, eamc
-    from paper_2011_08560_gb300.workloads import UNEVEN
     stream = torch.cuda.Stream()
-    ctx = eamc.Context(seed=UNEVEN["seed"], device=0, stream=stream.cuda_stream)
-    Ls = UNEVEN["Ls"]
-    groups, one_over_k = [], []
-    for kind_idx, kind in enumerate((eamc.EA_POWERLAW, eamc.EA_FLAT, eamc.EA_ONE_OVER_K)):
-        for L in Ls:
-            # realization ids with L = Ls[id % 5] are a contiguous block after sorting by L
-            n = sum(1 for r in range(UNEVEN["n_real"]) if Ls[r % len(Ls)] == L)
-            first = ctx.init_disorder(3, L, n, rid0=Ls.index(L) * UNEVEN["n_real"], stream=kind_idx)
-            ctx.set_ensemble(first, n, eamc.EA_POWERLAW if kind == eamc.EA_POWERLAW else eamc.EA_FLAT)
-            if kind == eamc.EA_ONE_OVER_K:
-                one_over_k.append((first, n))
-            groups.append((3, L, n))
-    best = autotune.apply(ctx, groups, sweeps=20)
-    # one iteration step, then the 1/k chains take 1/k weights built from their estimate
-    ctx.run_sweeps(S, count_roundtrips=False)
-    ctx.update_weights()
-    for first, n in one_over_k:
-        ctx.build_ensemble(first, n, eamc.EA_ONE_OVER_K)
+    ctx, groups, best = build_uneven(eamc, autotune, stream.cuda_stream, S)
     attempts_per_sweep = sum(n * L ** 3 for _, L, n in groups)
     ctx.graph_capture(n_iter=iters, sweeps_per_iter=S, count_roundtrips=True, update_weights=True)
     ctx.graph_launch(1)
