@@ -124,6 +124,8 @@ __device__ __forceinline__ uint32_t quantize_prob(double p) {
     return (q >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)q;
 }
 
+constexpr int kTailQ = 32;  // open comparisons a warp defers per colour phase
+
 struct PtArgs {
     uint32_t *spins;
     const uint32_t *bonds;
@@ -160,7 +162,11 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
     int32_t *Es = (int32_t *)(J + NB);      // [spc][32]
     int32_t *Ls = Es + spc * 32;            // [spc][32]
     uint32_t *Amask = (uint32_t *)(Ls + spc * 32);  // [spc] exchange masks of owned pairs
-    int32_t *Cl = (int32_t *)(Amask + spc); // odd L: sites by colour [V], then offsets [4]
+    // per-warp queue of site words whose comparison is still open after 8 planes:
+    // [nwarps][kTailQ] x (site | slot << 16, acc, und, C0, C1, C2)
+    uint32_t *TQ = Amask + spc;
+    int32_t *Ep = (int32_t *)(TQ + nwarps * kTailQ * 6);   // [nwarps][spc][32] partial counts
+    int32_t *Cl = Ep + nwarps * spc * 32;  // odd L: sites by colour [V], then offsets [4]
 
     const uint32_t group_rid0 = a.rid0 + 32u * (uint32_t)g;
     const int nvalid = min(32, a.n_real - 32 * g);
@@ -192,8 +198,29 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         const uint64_t t = a.t0 + s;
         const uint32_t tt = (uint32_t)t;
         // ---- checkerboard Metropolis sweep of every owned slot
+        // planes 8..31 of one site word: drawn only while a bit is still undecided
+        auto finish = [&](int i, int ks, uint32_t C0, uint32_t C1, uint32_t C2, uint32_t acc, uint32_t und) {
+            const uint32_t c2 = (uint32_t)g + (a.rid0 >> 5), c3 = 4u | ((uint32_t)(k0 + ks) << 8);
+            const uint4 *Pk = P + ks * 32;
+            uint4 w4 = make_uint4(0, 0, 0, 0);
+            for (int m = 8; m < 32 && und; ++m) {
+                if ((m & 3) == 0)
+                    w4 = philox4x32_10(make_uint4((uint32_t)(8 * i + (m >> 2)), tt, c2, c3), a.key);
+                const uint32_t R = uint4_get(w4, m & 3);
+                const uint4 q = Pk[m];
+                const uint32_t Tm = (C0 & q.x) | (C1 & q.y) | (C2 & q.z);
+                acc |= und & ~R & Tm;
+                und &= ~(R ^ Tm);
+            }
+            return acc;
+        };
+        uint32_t *tq = TQ + warp * kTailQ * 6;
         for (int colour = 0; colour < NCOL; ++colour) {
             const int nc = ((L & 1) == 0) ? HALF : Cl[V + colour + 1] - Cl[V + colour];
+            // site words of one colour never neighbour each other, so a word whose comparison
+            // is still open after 8 planes (about 6 % of them) can be finished after the others:
+            // the warp queues them and finishes them together, one per lane
+            int nq = 0;
             for (int item = tid; item < spc * nc; item += blockDim.x) {
                 const int ks = item / nc, j = item % nc;
                 int i;
@@ -252,25 +279,47 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                     acc |= und & ~Rm[m] & Tm;  // r bit 0, threshold bit 1: r < threshold
                     und &= ~(Rm[m] ^ Tm);      // equal bits: still undecided
                 }
-                uint4 w4 = make_uint4(0, 0, 0, 0);
-                for (int m = 8; m < 32 && und; ++m) {
-                    if ((m & 3) == 0)
-                        w4 = philox4x32_10(make_uint4((uint32_t)(8 * i + (m >> 2)), tt, c2, c3), a.key);
-                    const uint32_t R = uint4_get(w4, m & 3);
-                    const uint4 q = Pk[m];
-                    const uint32_t Tm = (C[0] & q.x) | (C[1] & q.y) | (C[2] & q.z);
-                    acc |= und & ~R & Tm;
-                    und &= ~(R ^ Tm);
+                (void)c2;
+                (void)c3;
+                // the lanes of this warp that have an item in this round (items are consecutive)
+                const int rem = spc * nc - (item - lane);
+                const uint32_t live = rem >= 32 ? kFull : ((1u << rem) - 1u);
+                const bool open = und != 0u;
+                const uint32_t om = __ballot_sync(live, open);
+                const int pos = nq + __popc(om & ((1u << lane) - 1u));
+                const bool deferred = open && pos < kTailQ;
+                if (deferred) {
+                    uint32_t *e = tq + pos * 6;
+                    e[0] = (uint32_t)i | ((uint32_t)ks << 16);
+                    e[1] = acc;
+                    e[2] = und;
+                    e[3] = C[0];
+                    e[4] = C[1];
+                    e[5] = C[2];
+                } else {
+                    if (open) acc = finish(i, ks, C[0], C[1], C[2], acc, und);  // queue full
+                    Sk[i] = si ^ (acc & valid);
                 }
-                Sk[i] = si ^ (acc & valid);
+                nq += __popc(om);
+            }
+            __syncwarp();
+            nq = __shfl_sync(kFull, nq, 0);
+            for (int e0 = 0; e0 < min(nq, kTailQ); e0 += 32) {
+                const int e = e0 + lane;
+                if (e < min(nq, kTailQ)) {
+                    const uint32_t *q = tq + e * 6;
+                    const int i = (int)(q[0] & 0xFFFFu), ks = (int)(q[0] >> 16);
+                    const uint32_t acc = finish(i, ks, q[3], q[4], q[5], q[1], q[2]);
+                    S[ks * V + i] ^= acc & valid;
+                }
             }
             __syncthreads();
         }
-        // ---- energies of the owned slots: u_b = number of unsatisfied bonds of bit b
-        for (int k = tid; k < spc * 32; k += blockDim.x) Es[k] = 0;
-        __syncthreads();
+        // ---- energies of the owned slots: u_b = number of unsatisfied bonds of bit b; every
+        //      warp leaves its partial counts in Ep, one barrier, then they are summed
         for (int ks = 0; ks < spc; ++ks) {
             const uint32_t *Sk = S + ks * V;
+            int part = 0;
             for (int base = warp * 32; base < V; base += nwarps * 32) {
                 const int i = base + lane;
                 uint32_t c0 = 0, c1 = 0;  // bit-sliced count (0..3) of this site's +d bonds
@@ -283,14 +332,17 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                     }
                 }
                 const uint32_t t0w = warp_transpose(c0, lane), t1w = warp_transpose(c1, lane);
-                const int cnt = __popc(t0w) + 2 * __popc(t1w);
-                atomicAdd(&Es[ks * 32 + lane], cnt);
+                part += __popc(t0w) + 2 * __popc(t1w);
             }
+            Ep[(warp * spc + ks) * 32 + lane] = part;
         }
         __syncthreads();
-        for (int k = tid; k < spc * 32; k += blockDim.x) Es[k] = 2 * Es[k] - NB;
-        __syncthreads();
-        cluster.sync();  // every slot's energy is known
+        for (int k = tid; k < spc * 32; k += blockDim.x) {
+            int u = 0;
+            for (int w = 0; w < nwarps; ++w) u += Ep[w * spc * 32 + k];
+            Es[k] = 2 * u - NB;
+        }
+        cluster.sync();  // every slot's energy is known (and a barrier of this CTA)
         // ---- replica exchange between (k, k+1), k = t mod 2 (mod 2); the owner of k decides
         if (warp == 0) {
             for (int ks = 0; ks < spc; ++ks) {
@@ -464,8 +516,10 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
     a.n_sweeps = n_sweeps;
     a.count_rt = count_rt;
     a.key = ctx->key;
+    const int items = a.spc * (G::V / 2);
+    const int threads = std::min(256, std::max(64, (items + 31) / 32 * 32));
     const size_t smem = (size_t)(a.spc * 128 + a.spc * G::V + G::NB + a.spc * 32 * 2 + a.spc +
-                                 ((L & 1) ? G::V + 4 : 0)) * 4;
+                                 (threads / 32) * (kTailQ * 6 + a.spc * 32) + ((L & 1) ? G::V + 4 : 0)) * 4;
     cudaError_t e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -475,8 +529,7 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
     cfg.gridDim = dim3(p->n_groups * p->cs);
     // up to one thread per site of one colour of the CTA's slots (at most 256, at least 2
     // warps); 512-thread blocks measured slower (barrier cost, register cap)
-    const int items = a.spc * (G::V / 2);
-    cfg.blockDim = dim3(std::min(256, std::max(64, (items + 31) / 32 * 32)));
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
