@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
     // [nwarps][kTailQ] x (site | slot << 16, acc, und, C0, C1, C2)
     uint32_t *TQ = Amask + spc;
     int32_t *Ep = (int32_t *)(TQ + nwarps * kTailQ * 6);   // [nwarps][spc][32] partial counts
-    int32_t *Cl = Ep + nwarps * spc * 32;  // odd L: sites by colour [V], then offsets [4]
+    uint32_t *Xc = (uint32_t *)(Ep + nwarps * spc * 32);  // [spc][32] accepted exchanges, this launch
+    int32_t *Bd = (int32_t *)(Xc + spc * 32);             // [32][2] round-trip bounds (e_g, e_hot)
+    double *Db = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(Bd + 64) + 7) & ~uintptr_t(7));  // [spc][32]
+    int32_t *Cl = (int32_t *)(Db + spc * 32);  // odd L: sites by colour [V], then offsets [4]
 
     const uint32_t group_rid0 = a.rid0 + 32u * (uint32_t)g;
     const int nvalid = min(32, a.n_real - 32 * g);
@@ -180,6 +183,14 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         Ls[k] = a.label[((size_t)g * M + k0) * 32 + k];
     }
     for (int k = tid; k < spc * 128; k += blockDim.x) sm[k] = a.planes[((size_t)g * M + k0) * 128 + k];
+    // per launch: beta_{k+1} - beta_k of every owned pair and realization, the round-trip bounds,
+    // zeroed exchange counters (added to the global ones at the end)
+    for (int q = tid; q < spc * 32; q += blockDim.x) {
+        const int k = k0 + (q >> 5), b = q & 31;
+        Db[q] = (k + 1 < M) ? a.beta[((size_t)g * M + k + 1) * 32 + b] - a.beta[((size_t)g * M + k) * 32 + b] : 0.0;
+        Xc[q] = 0u;
+    }
+    for (int q = tid; q < 64; q += blockDim.x) Bd[q] = a.bounds[(size_t)g * 64 + q];
     if constexpr ((L & 1) != 0) {
         if (tid == 0) {  // colour classes in lexicographic order (a few thousand steps per launch)
             int n = 0;
@@ -343,9 +354,10 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
             Es[k] = 2 * u - NB;
         }
         cluster.sync();  // every slot's energy is known (and a barrier of this CTA)
-        // ---- replica exchange between (k, k+1), k = t mod 2 (mod 2); the owner of k decides
-        if (warp == 0) {
-            for (int ks = 0; ks < spc; ++ks) {
+        // ---- replica exchange between (k, k+1), k = t mod 2 (mod 2); the owner of k decides,
+        //      one warp per owned slot
+        {
+            for (int ks = warp; ks < spc; ks += nwarps) {
                 const int k = k0 + ks;
                 uint32_t A = 0u;
                 if (((k ^ (int)t) & 1) == 0 && k + 1 < M) {
@@ -359,15 +371,12 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                     } else {
                         // Eq. "temperatureexchange" with this realization's beta_k, beta_k+1
                         const int d = (e0 - e1) / 4;
-                        const double b0 = a.beta[((size_t)g * M + k) * 32 + lane];
-                        const double b1 = a.beta[((size_t)g * M + k + 1) * 32 + lane];
-                        const uint32_t th = quantize_prob(exp(-(b1 - b0) * 4.0 * (double)d));
+                        const uint32_t th = quantize_prob(exp(-Db[ks * 32 + lane] * 4.0 * (double)d));
                         const uint4 w = philox4x32_10(make_uint4((uint32_t)k, tt, group_rid0 + lane, 1u), a.key);
                         ok = (th == kAlways) || (w.x < th);
                     }
                     A = __ballot_sync(kFull, ok) & valid;
-                    if ((A >> lane) & 1u) a.xacc[((size_t)g * M + k) * 32 + lane] += 1u;
-                    if (lane == 0 && A) atomicAdd(&a.swaps[k], (unsigned long long)__popc(A));
+                    Xc[ks * 32 + lane] += (A >> lane) & 1u;
                 }
                 if (lane == 0) Amask[ks] = A;
             }
@@ -405,8 +414,8 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
             PtRt &r = a.rt[((size_t)g * M + lbl) * 32 + b];
             if (E < r.e_min) r.e_min = E;
             if (a.count_rt) {
-                const int eg = a.bounds[((size_t)g * 32 + b) * 2 + 0];
-                const int ehot = a.bounds[((size_t)g * 32 + b) * 2 + 1];
+                const int eg = Bd[2 * b + 0];
+                const int ehot = Bd[2 * b + 1];
                 if (r.phase == 0) {
                     if (E >= ehot) { r.t_first = (int64_t)t; r.phase = 1; }
                 } else if (r.phase == 1) {
@@ -420,6 +429,13 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         __syncthreads();
     }
     // ---- write back
+    for (int q = tid; q < spc * 32; q += blockDim.x) {
+        const int k = k0 + (q >> 5);
+        if (Xc[q]) {
+            a.xacc[((size_t)g * M + k) * 32 + (q & 31)] += Xc[q];
+            atomicAdd(&a.swaps[k], (unsigned long long)Xc[q]);
+        }
+    }
     for (int k = tid; k < spc * V; k += blockDim.x) a.spins[((size_t)g * M + k0) * V + k] = S[k];
     for (int k = tid; k < spc * 32; k += blockDim.x) {
         a.E[((size_t)g * M + k0) * 32 + k] = Es[k];
@@ -519,7 +535,8 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
     const int items = a.spc * (G::V / 2);
     const int threads = std::min(256, std::max(64, (items + 31) / 32 * 32));
     const size_t smem = (size_t)(a.spc * 128 + a.spc * G::V + G::NB + a.spc * 32 * 2 + a.spc +
-                                 (threads / 32) * (kTailQ * 6 + a.spc * 32) + ((L & 1) ? G::V + 4 : 0)) * 4;
+                                 (threads / 32) * (kTailQ * 6 + a.spc * 32) + a.spc * 32 + 64 + 1 + 2 * a.spc * 32 +
+                                 ((L & 1) ? G::V + 4 : 0)) * 4;
     cudaError_t e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
