@@ -169,7 +169,11 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
     uint32_t *Xc = (uint32_t *)(Ep + nwarps * spc * 32);  // [spc][32] accepted exchanges, this launch
     int32_t *Bd = (int32_t *)(Xc + spc * 32);             // [32][2] round-trip bounds (e_g, e_hot)
     double *Db = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(Bd + 64) + 7) & ~uintptr_t(7));  // [spc][32]
-    int32_t *Cl = (int32_t *)(Db + spc * 32);  // odd L: sites by colour [V], then offsets [4]
+    // round-trip records of the replica labels k0 .. k0+spc-1 ("home" labels of this CTA), for
+    // the launch; a label's record is updated by whichever CTA holds that replica, through
+    // distributed shared memory
+    PtRt *Rh = reinterpret_cast<PtRt *>(Db + spc * 32);    // [spc][32]
+    int32_t *Cl = (int32_t *)(Rh + spc * 32);  // odd L: sites by colour [V], then offsets [4]
 
     const uint32_t group_rid0 = a.rid0 + 32u * (uint32_t)g;
     const int nvalid = min(32, a.n_real - 32 * g);
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         Xc[q] = 0u;
     }
     for (int q = tid; q < 64; q += blockDim.x) Bd[q] = a.bounds[(size_t)g * 64 + q];
+    for (int q = tid; q < spc * 32; q += blockDim.x) Rh[q] = a.rt[((size_t)g * M + k0) * 32 + q];
     if constexpr ((L & 1) != 0) {
         if (tid == 0) {  // colour classes in lexicographic order (a few thousand steps per launch)
             int n = 0;
@@ -411,7 +416,7 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
             const int ks = q >> 5, b = q & 31;
             if (!((valid >> b) & 1u)) continue;
             const int lbl = Ls[q], E = Es[q];
-            PtRt &r = a.rt[((size_t)g * M + lbl) * 32 + b];
+            PtRt &r = cluster.map_shared_rank(Rh, lbl / spc)[(lbl % spc) * 32 + b];
             if (E < r.e_min) r.e_min = E;
             if (a.count_rt) {
                 const int eg = Bd[2 * b + 0];
@@ -428,7 +433,9 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
         }
         __syncthreads();
     }
-    // ---- write back
+    // ---- write back (every CTA of the cluster is done with this CTA's records)
+    cluster.sync();
+    for (int q = tid; q < spc * 32; q += blockDim.x) a.rt[((size_t)g * M + k0) * 32 + q] = Rh[q];
     for (int q = tid; q < spc * 32; q += blockDim.x) {
         const int k = k0 + (q >> 5);
         if (Xc[q]) {
@@ -536,7 +543,7 @@ cudaError_t pt_launch_all(PtState *p, const int8_t *dJ, ea_ctx *ctx, int what, u
     const int threads = std::min(256, std::max(64, (items + 31) / 32 * 32));
     const size_t smem = (size_t)(a.spc * 128 + a.spc * G::V + G::NB + a.spc * 32 * 2 + a.spc +
                                  (threads / 32) * (kTailQ * 6 + a.spc * 32) + a.spc * 32 + 64 + 1 + 2 * a.spc * 32 +
-                                 ((L & 1) ? G::V + 4 : 0)) * 4;
+                                 a.spc * 32 * (int)(sizeof(PtRt) / 4) + ((L & 1) ? G::V + 4 : 0)) * 4;
     cudaError_t e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(pt_kernel<DIM, L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
