@@ -379,28 +379,43 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         const bool next_uym = (DIM == 2 || y_next > 0);
 #pragma unroll
         for (int x = 0; x < L; ++x) {
-            const uint32_t th = pa ? thB : thA;
-            const int rx = pa ? rq + dq : rq;
-            const int dx = (DIM - (pa ? nB : nA)) * RSB;
+            // what does not depend on the previous decision comes first: both candidate deltas
+            // of this attempt and all four candidate addresses of the next attempt's loads; the
+            // previous decision then only selects
+            const int rB = rq + dq;
+            const int dxA = (DIM - nA) * RSB, dxB = (DIM - nB) * RSB;
+            int nA1 = 0, nB1 = 0;
+            bool next = false;
             if (x + 1 < L) {
-                nA = (int)((sA >> (4 * (x + 1))) & 0xF);
-                nB = (int)((sB >> (4 * (x + 1))) & 0xF);
+                nA1 = (int)((sA >> (4 * (x + 1))) & 0xF);
+                nB1 = (int)((sB >> (4 * (x + 1))) & 0xF);
                 if (x + 1 == L - 1) {  // bond to site 0 of the row, flipped at x = 0 or not
                     const int w = wbit ^ (int)(accN & 1u);
-                    nA += w;
-                    nB += w;
+                    nA1 += w;
+                    nB1 += w;
                 }
-                thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + nA * NSB));
-                thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + dx + nB * NSB));
+                next = true;
             } else if (LAG >= 2 && k + 1 < total) {
                 // first attempt of the next row: its class needs that row's record and, through
                 // the -y bond, only site 0 of this row (final since attempt 0); both candidate
                 // bins depend on this attempt
                 const T rfin0 = (R ^ accN) & T(1);
-                const int n0 = (int)(nsA & 0xF) + (next_uym ? (int)((nR ^ rfin0 ^ njym) & T(1)) : 0);
-                thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + n0 * NSB));
-                thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + rx + dx + n0 * NSB));
+                nA1 = nB1 = (int)(nsA & 0xF) + (next_uym ? (int)((nR ^ rfin0 ^ njym) & T(1)) : 0);
+                next = true;
                 have_next = true;
+            }
+            const int offA = nA1 * NSB, offB = nB1 * NSB;
+            const int aA0 = rq + offA, aB0 = rq + dxA + offB, aA1 = rB + offA, aB1 = rB + dxB + offB;
+            const uint32_t th = pa ? thB : thA;
+            const int rx = pa ? rB : rq;
+            const int dx = pa ? dxB : dxA;
+            if (next) {
+                thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + (pa ? aA1 : aA0)));
+                thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + (pa ? aB1 : aB0)));
+            }
+            if (x + 1 < L) {
+                nA = nA1;
+                nB = nB1;
             }
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
             const bool acc = active && (th == kAlways || r < th);
