@@ -45,7 +45,7 @@ ALG_OPS_PER_ATTEMPT = 21.5
 PT_ALG_OPS = 4.7
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch of the headline workload
 # (ncu, profiles/muca_sweep_L6_2048chains.md)
-SWEEP_TRAFFIC_BYTES = 11.60e6
+SWEEP_TRAFFIC_BYTES = 11.61e6
 
 
 def parse():
