@@ -241,6 +241,12 @@ def run_gpu(args, rank, world):
         t_ms = reduce_max_ms(t_ms, world, device="cuda")
         torch.distributed.barrier()
     rts = total_rt(ctx) - rt0
+    # mean round-trip time in sweeps (Sec. III: tau_i = (t_last - t_first) / n_rt) of the chains
+    # with a round trip so far, by ensemble; the weights iterate once per step meanwhile
+    taus = {"flat": [], "power_law": []}
+    for c, rec in enumerate(ctx.roundtrips()):
+        if rec["n_rt"] > 0:
+            taus["flat" if c < W.n_real else "power_law"].append((rec["t_last"] - rec["t_first"]) / rec["n_rt"])
     value = world * attempts_per_step * args.steps / (t_ms * 1e6)
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     achieved_ops = attempts_per_step * ALG_OPS_PER_ATTEMPT / kern_avg_s
@@ -276,8 +282,19 @@ def run_gpu(args, rank, world):
         "rts": rts, "attempts_per_step": attempts_per_step, "n_chains": n_chains,
         "achieved_ops": achieved_ops, "alu_peak": alu_peak, "clocks": clk.summary(),
         "e2e_ms": statistics.median(e2e_ms), "h2d": h2d, "d2h": d2h, "plain": plain,
-        "sm_count": props.multi_processor_count,
+        "sm_count": props.multi_processor_count, "taus": taus,
     }
+
+
+def rt_roofline(r, world):
+    all_taus = r["taus"]["flat"] + r["taus"]["power_law"]
+    if not all_taus:
+        return None
+    V = HEADLINE.L ** HEADLINE.dim
+    peak = world * r["alu_peak"] / ALG_OPS_PER_ATTEMPT / (V * statistics.mean(all_taus))
+    achieved = world * r["rts"] / (r["t_ms"] / 1e3)
+    return {"achieved": achieved, "peak": peak, "unit": "round trips/s", "frac": achieved / peak,
+            "basis": "ALU peak / ops per attempt / (V x mean round-trip time in sweeps)"}
 
 
 def plain_form(eamc, stream, S: int):
@@ -490,8 +507,8 @@ def bench_recursion(L: int = 8, n: int = 256, iters: int = 24, S: int = 2000, P:
     return out
 
 
-def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 40, dos_sweeps: int = 4000,
-                       prod_sweeps: int = 20000):
+def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_sweeps: int = 10000,
+                       prod_sweeps: int = 100000):
     """Profile-parameter scan (Sec. II): power-law alpha x Delta E grid, flat and 1/k beside
     it, n_real realizations of L^3, density of states once per realization (power-law target,
     Berg's recursion), production with round-trip counting in one batched launch.  Reports the
@@ -596,6 +613,11 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded +-J disorder, random initial spins)", "config": config,
         "round_trips_per_s": world * r["rts"] / (r["t_ms"] / 1e3),
+        "round_trip_time_sweeps": {
+            k: {"mean": statistics.mean(v) if v else None, "chains_with_round_trip": len(v)}
+            for k, v in r["taus"].items()},
+        # round trips/s against the ALU roofline: attempts/s at the roofline / (V x mean tau)
+        "round_trips_roofline": rt_roofline(r, world),
         "plain_form": r["plain"],
         "e2e": {"value": attempts_e2e / (r["e2e_ms"] * 1e6), "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
