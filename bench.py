@@ -39,6 +39,10 @@ UNIT = "attempts/ns"
 # plus extraction) + 3 (threshold fetch and compare) + 2 (flip and energy update)
 # + 3 (lowest energy and round-trip check)
 ALG_OPS_PER_ATTEMPT = 21.5
+# per-chain latency floor of one MUCA attempt in SM cycles: with the next attempt's candidate
+# thresholds loaded one attempt ahead, two attempts cost one address select, one shared-memory
+# load (about 29 cycles, measured) and the compare / select of the decision, about 40 cycles
+LATENCY_FLOOR_CYCLES = 20.0
 # PT, per site word of 32 lattices (32 attempts): 12 word loads + 14 bit ops for the
 # unsatisfied counts + 4 for the classes, about 8 compared bit planes (2 Philox4x32-10 calls of
 # 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
@@ -282,7 +286,7 @@ def run_gpu(args, rank, world):
         "rts": rts, "attempts_per_step": attempts_per_step, "n_chains": n_chains,
         "achieved_ops": achieved_ops, "alu_peak": alu_peak, "clocks": clk.summary(),
         "e2e_ms": statistics.median(e2e_ms), "h2d": h2d, "d2h": d2h, "plain": plain,
-        "sm_count": props.multi_processor_count, "taus": taus,
+        "sm_count": props.multi_processor_count, "taus": taus, "sm_max_mhz": sm_max,
     }
 
 
@@ -618,6 +622,15 @@ def main():
             for k, v in r["taus"].items()},
         # round trips/s against the ALU roofline: attempts/s at the roofline / (V x mean tau)
         "round_trips_roofline": rt_roofline(r, world),
+        # the bound that applies to a batch of serial chains: every chain needs at least
+        # LATENCY_FLOOR_CYCLES per attempt (select + shared-memory load + compare, loads issued
+        # one attempt ahead), so attempts/ns <= chains x SM clock / floor
+        "latency_roofline": {"achieved": r["value"],
+                             "peak": world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / LATENCY_FLOOR_CYCLES,
+                             "unit": UNIT,
+                             "frac": r["value"] / (world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / LATENCY_FLOOR_CYCLES),
+                             "cycles_per_attempt_floor": LATENCY_FLOOR_CYCLES,
+                             "cycles_per_attempt_achieved": world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / r["value"]},
         "plain_form": r["plain"],
         "e2e": {"value": attempts_e2e / (r["e2e_ms"] * 1e6), "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
