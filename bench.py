@@ -245,6 +245,11 @@ def run_gpu(args, rank, world):
         t_ms = reduce_max_ms(t_ms, world, device="cuda")
         torch.distributed.barrier()
     rts = total_rt(ctx) - rt0
+    try:
+        ctx.check()                       # device-side invariants held during the timed steps
+        invariants = "ok"
+    except eamc.EamcError as err:
+        invariants = str(err)
     # mean round-trip time in sweeps (Sec. III: tau_i = (t_last - t_first) / n_rt) of the chains
     # with a round trip so far, by ensemble; the weights iterate once per step meanwhile
     taus = {"flat": [], "power_law": []}
@@ -287,6 +292,7 @@ def run_gpu(args, rank, world):
         "achieved_ops": achieved_ops, "alu_peak": alu_peak, "clocks": clk.summary(),
         "e2e_ms": statistics.median(e2e_ms), "h2d": h2d, "d2h": d2h, "plain": plain,
         "sm_count": props.multi_processor_count, "taus": taus, "sm_max_mhz": sm_max,
+        "invariants": invariants,
     }
 
 
@@ -617,6 +623,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded +-J disorder, random initial spins)", "config": config,
         "round_trips_per_s": world * r["rts"] / (r["t_ms"] / 1e3),
+        "invariant_check": r["invariants"],
         "round_trip_time_sweeps": {
             k: {"mean": statistics.mean(v) if v else None, "chains_with_round_trip": len(v)}
             for k, v in r["taus"].items()},

@@ -235,6 +235,13 @@ int ea_snapshot_size(ea_ctx *ctx, size_t *bytes);
 int ea_snapshot_save(ea_ctx *ctx, void *buf, size_t cap);
 int ea_snapshot_load(ea_ctx *ctx, const void *buf, size_t size);
 
+/* Invariant check (the role a sanitizer would have; not in the paper): while sweeping, the
+ * kernel checks off the critical path that every chain's energy stays inside its range
+ * [E_min of the table, E_top], i.e. its bin inside [0, b_top].  Waits for the context's work,
+ * returns EA_ESTATE (message in ea_last_error) if a check failed since the last call, EA_OK
+ * otherwise, and clears the record. */
+int ea_check(ea_ctx *ctx);
+
 /* Waits for all queued work of the context. */
 int ea_synchronize(ea_ctx *ctx);
 

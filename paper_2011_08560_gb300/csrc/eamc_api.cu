@@ -313,11 +313,14 @@ extern "C" int ea_create(ea_ctx **out, int device, void *cuda_stream, uint64_t s
     if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaMalloc"); }
     cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
     cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&ctx->d_queue, sizeof(int)) != cudaSuccess) {
+    // d_queue[0]: work-queue counter of persistent sweeps; d_queue[1]: invariant flags set by
+    // the sweep kernel (read and cleared by ea_check)
+    if (cudaMalloc(&ctx->d_queue, 2 * sizeof(int)) != cudaSuccess) {
         cudaFree(ctx->d_err);
         delete ctx;
         return fail(EA_ENOMEM, "queue allocation failed");
     }
+    cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(int), ctx->stream);
     *out = ctx;
     return EA_OK;
 }
@@ -633,11 +636,11 @@ static int enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) 
             const int grid = std::min(nt, per_sm * std::max(ctx->n_sm, 1));
             EA_CUDA(launch_sweeps(ctx->d_tiles, ctx->d_order, grid, nt, ctx->d_queue, ctx->dim, ctx->sweep_smem,
                                   ctx->d_slots, ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key,
-                                  count_roundtrips, ctx->stream));
+                                  count_roundtrips, reinterpret_cast<unsigned *>(ctx->d_queue + 1), ctx->stream));
         } else {
             EA_CUDA(launch_sweeps(ctx->d_tiles, nullptr, nt, nt, nullptr, ctx->dim, ctx->sweep_smem, ctx->d_slots,
                                   ctx->d_spins, ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key,
-                                  count_roundtrips, ctx->stream));
+                                  count_roundtrips, reinterpret_cast<unsigned *>(ctx->d_queue + 1), ctx->stream));
         }
     }
     return EA_OK;
@@ -952,6 +955,16 @@ extern "C" int get_state(ea_ctx *ctx, int chain0, int n, int8_t *spins, int stri
         if (E) E[k] = h[k].E;
         if (t) t[k] = h[k].t;
     }
+    return EA_OK;
+}
+
+extern "C" int ea_check(ea_ctx *ctx) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    unsigned flags = 0u;
+    EA_CUDA(cudaMemcpyAsync(&flags, ctx->d_queue + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CUDA(cudaMemsetAsync(ctx->d_queue + 1, 0, sizeof(unsigned), ctx->stream));
+    EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (flags & 1u) return fail(EA_ESTATE, "a chain left its energy range [0, b_top] during a sweep");
     return EA_OK;
 }
 

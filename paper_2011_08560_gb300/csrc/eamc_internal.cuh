@@ -63,7 +63,7 @@ size_t sweep_smem_bytes(int dim, int L);  // dynamic shared memory of a tile of 
 cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, int n_blocks, int n_work,
                           int *d_queue, int dim, size_t smem, SlotState *d_slots, uint32_t *d_spins,
                           const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
-                          PhiloxKey key, int count_rt, cudaStream_t st);
+                          PhiloxKey key, int count_rt, unsigned *d_diag, cudaStream_t st);
 int sweep_blocks_per_sm(int dim, size_t smem);
 cudaError_t prepare_sweeps(int dim, size_t smem);  // resident sweep blocks per SM at this smem
 cudaError_t launch_quantize(const TileDesc *d_tiles, int n_tiles, const SlotState *d_slots,

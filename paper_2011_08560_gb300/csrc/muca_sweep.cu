@@ -142,7 +142,8 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
                                            const uint32_t *__restrict__ bonds,
                                            const uint32_t *__restrict__ thr,
                                            uint32_t *__restrict__ hist, uint64_t n_sweeps,
-                                           PhiloxKey key, int count_rt, unsigned char *smem_raw) {
+                                           PhiloxKey key, int count_rt, unsigned *__restrict__ diag,
+                                           unsigned char *smem_raw) {
     using G = Geo<DIM, L>;
     using T = typename G::T;
     constexpr int NR = G::NR, LAG = G::LAG, NBUF = G::NBUF;
@@ -268,19 +269,22 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         uint32_t *hist_l = hist + lrow;
         int mrow = 0;
         uint64_t ms = 0;
+        bool out_of_range = false;  // a bin outside [0, b_top]: a broken invariant, reported via diag
         auto measure = [&](int buf) {
             const int *r = res + buf * L * 32 + lane;
-            int lo = 0x7FFFFFFF;
+            int lo = 0x7FFFFFFF, hi = -0x7FFFFFFF;
             uint32_t mtop = 0u, mbot = 0u;
 #pragma unroll
             for (int x = 0; x < L; ++x) {
                 const int pr = r[x * 32];
                 lo = min(lo, pr);
+                hi = max(hi, pr);
                 mtop |= (uint32_t)(pr >= topB) << x;
                 mbot |= (uint32_t)(pr <= botB) << x;
                 if (x == L - 1) pnow = pr;
             }
             pmin = min(pmin, lo);
+            out_of_range |= (lo < 0) | (hi > topB);
             // the attempts of the row in order: a transition at the first attempt that meets
             // the current phase's condition (E <= E_g heading down, E >= E_top otherwise), the
             // next one looked for after it
@@ -324,6 +328,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             ss.t = t0 + n_sweeps;
             if (count_rt && active && energy_of_bin(DIM * G::V, ss.parity, ss.b_min) < ss.e_g) ss.requeue = 1;
             slots[slot] = ss;
+            if (diag && __any_sync(kFull, active && out_of_range) && lane == 0) atomicOr(diag, 1u);
         }
         return;
     }
@@ -454,13 +459,13 @@ template <int DIM>
 __device__ __forceinline__ void sweep_one(const TileDesc *__restrict__ tiles, int tile, SlotState *slots,
                                           uint32_t *spins, const uint32_t *bonds, const uint32_t *thr,
                                           uint32_t *hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
-                                          unsigned char *smem_raw) {
+                                          unsigned *diag, unsigned char *smem_raw) {
     const TileDesc td = tiles[tile];
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CASE(LL)                                                                      \
     case LL:                                                                               \
-        sweep_tile<DIM, LL>(td, tile, slots, spins, bonds, thr, hist, n_tile, key, count_rt, \
-                            smem_raw);                                                     \
+        sweep_tile<DIM, LL>(td, tile, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, \
+                            smem_raw);                                                           \
         break;
     switch (td.L) {
         EAMC_CASE(3) EAMC_CASE(4) EAMC_CASE(5) EAMC_CASE(6) EAMC_CASE(7)
@@ -475,11 +480,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ tile_list, int n_work,
                   int *__restrict__ queue, SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
                   const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
-                  uint32_t *__restrict__ hist, uint64_t n_sweeps, PhiloxKey key, int count_rt) {
+                  uint32_t *__restrict__ hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
+                  unsigned *__restrict__ diag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!queue) {
         const int tile = tile_list ? tile_list[blockIdx.x] : (int)blockIdx.x;
-        sweep_one<DIM>(tiles, tile, slots, spins, bonds, thr, hist, n_sweeps, key, count_rt, smem_raw);
+        sweep_one<DIM>(tiles, tile, slots, spins, bonds, thr, hist, n_sweeps, key, count_rt, diag, smem_raw);
         return;
     }
     __shared__ int s_pos;
@@ -489,7 +495,7 @@ muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict_
         const int pos = s_pos;
         __syncthreads();  // every thread has read s_pos before it is overwritten
         if (pos >= n_work) break;
-        sweep_one<DIM>(tiles, tile_list[pos], slots, spins, bonds, thr, hist, n_sweeps, key, count_rt,
+        sweep_one<DIM>(tiles, tile_list[pos], slots, spins, bonds, thr, hist, n_sweeps, key, count_rt, diag,
                        smem_raw);
         __syncthreads();  // every warp is done with this tile's shared memory
     }
@@ -531,7 +537,7 @@ cudaError_t prepare_sweeps(int dim, size_t smem) {
 cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, int n_blocks, int n_work,
                           int *d_queue, int dim, size_t smem, SlotState *d_slots, uint32_t *d_spins,
                           const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
-                          PhiloxKey key, int count_rt, cudaStream_t st) {
+                          PhiloxKey key, int count_rt, unsigned *d_diag, cudaStream_t st) {
     if (n_blocks <= 0 || n_sweeps == 0) return cudaSuccess;
     cudaError_t e;
     if (d_queue) {
@@ -541,10 +547,10 @@ cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, i
     if ((e = prepare_sweeps(dim, smem)) != cudaSuccess) return e;
     if (dim == 3) {
         muca_sweep_kernel<3><<<n_blocks, kThreads, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
-                                                         d_bonds, d_thr, d_hist, n_sweeps, key, count_rt);
+                                                         d_bonds, d_thr, d_hist, n_sweeps, key, count_rt, d_diag);
     } else {
         muca_sweep_kernel<2><<<n_blocks, kThreads, smem, st>>>(d_tiles, d_tile_list, n_work, d_queue, d_slots, d_spins,
-                                                         d_bonds, d_thr, d_hist, n_sweeps, key, count_rt);
+                                                         d_bonds, d_thr, d_hist, n_sweeps, key, count_rt, d_diag);
     }
     return cudaGetLastError();
 }

@@ -200,7 +200,7 @@ extern "C" int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, con
                                                   d_spins, d_bonds, d_thr, d_err);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_sweeps(tiles, nullptr, n_tiles, n_tiles, nullptr, dim, smem, slots, d_spins, d_bonds,
-                          d_thr + kPad, hist, n_sweeps, key, 0, st));
+                          d_thr + kPad, hist, n_sweeps, key, 0, nullptr, st));
     if (dim == 3)
         unpack_kernel<3><<<n, 128, 0, st>>>(L, n, slots, d_spins, spins, energies);
     else

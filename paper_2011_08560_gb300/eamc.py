@@ -72,6 +72,7 @@ SIGNATURES = {
     "get_roundtrips": (_i, [P, _i, _i, P, _i]),
     "get_state": (_i, [P, _i, _i, P, _i, P, P]),
     "ea_synchronize": (_i, [P]),
+    "ea_check": (_i, [P]),
     "ea_snapshot_size": (_i, [P, P]),
     "ea_snapshot_save": (_i, [P, P, ctypes.c_size_t]),
     "ea_snapshot_load": (_i, [P, P, ctypes.c_size_t]),
@@ -255,6 +256,10 @@ class Context:
         t = np.zeros(n, dtype=np.uint64)
         check(lib().get_state(self._h, chain0, n, _p(S), V, _p(E), _p(t)))
         return S, E, t
+
+    def check(self):
+        """Raises EamcError if a sweep broke an invariant since the last check."""
+        check(lib().ea_check(self._h))
 
     def synchronize(self):
         check(lib().ea_synchronize(self._h))

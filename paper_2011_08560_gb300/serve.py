@@ -85,6 +85,7 @@ class Server:
         self.queue = collections.deque()
         self.active = {}              # chain -> Job
         self.done = []
+        self.cancelled = []
         self.ticks = 0
         self.attempts = 0
         self.n_rt_total = 0
@@ -114,6 +115,26 @@ class Server:
             raise ValueError(f"L={job.L} not served")
         job.phase = "queued"
         self.queue.append(job)
+
+    def cancel(self, jid: int) -> bool:
+        """Withdraws a job.  A waiting job leaves the queue; an admitted one gives its lane back
+        (the lane's chain keeps sweeping as an idle placeholder until the next admitted job
+        resets it in place, which leaves every other lane untouched).  Returns False when the
+        job is unknown or already finished."""
+        for j in list(self.queue):
+            if j.jid == jid:
+                self.queue.remove(j)
+                j.phase = "cancelled"
+                self.cancelled.append(j)
+                return True
+        for chain, j in list(self.active.items()):
+            if j.jid == jid:
+                del self.active[chain]
+                self.free[j.L].append(chain)
+                j.phase = "cancelled"
+                self.cancelled.append(j)
+                return True
+        return False
 
     def _admit(self, now: float):
         waiting = collections.deque()

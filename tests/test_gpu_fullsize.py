@@ -65,6 +65,7 @@ def test_headline_full_size_sampled(eamc, orc):
             ch.hist[:] = 0
             ch.rt.e_g = ch.rt.e_min          # the update takes E_g = the lowest energy seen
         _check(ctx, orc, stream_id * n + rid, ch, lnW)
+    ctx.check()                       # no chain left its energy range on the device
     ctx.close()
 
 
@@ -103,4 +104,5 @@ def test_uneven_full_size_sampled(eamc, orc):
                 ch.hist[:] = 0
             _check(ctx, orc, first + k, ch, lnW)
         first += n
+    ctx.check()
     ctx.close()

@@ -183,6 +183,7 @@ def test_weight_iteration_parity(eamc, orc, kind):
             assert _close(G[k, :c.b_top + 1], lnW[k]), (it, k)
             _thresholds_agree(orc, dim, T[k], lnW[k])
         _compare_state(ctx, chains, hist=True, rt=False)
+    ctx.check()
 
 
 @pytest.mark.parametrize("kind", [0, 1])

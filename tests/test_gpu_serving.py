@@ -85,3 +85,36 @@ def test_poisson_run_reports_latency(serve):
     assert stats["jobs"] == len(jobs) > 100
     assert stats["completed"] + stats["censored"] + stats["unfinished"] == stats["jobs"]
     assert stats["completed"] > 0 and stats["p99_s"] >= stats["p50_s"] > 0
+
+
+def test_cancel_frees_the_lane_for_an_exact_newcomer(serve):
+    """Cancelling a queued and a running job; the running job's lane is reused by a job whose
+    result equals the one it gets alone (the in-place reset leaves nothing behind)."""
+    probe = _job(serve, 0, 5, 777, 5)
+    alone = serve.Server(seed=31, Ls=(5,), base_sweeps=4)
+    a = copy.deepcopy(probe)
+    alone.submit(a)
+    _run_until(alone, a)
+    alone.close()
+
+    srv = serve.Server(seed=31, Ls=(5,), base_sweeps=4, mem_budget=serve.tile_bytes(3, 5))  # one tile
+    jobs = [_job(serve, 10 + k, 5, 900 + k, 10 ** 6) for k in range(34)]    # never finish
+    for j in jobs:
+        srv.submit(j)
+    for _ in range(5):
+        srv.tick()
+    assert len(srv.active) == 32 and len(srv.queue) == 2      # one tile of lanes, two waiting
+    running = next(iter(srv.active.values()))
+    lane = running.chain
+    assert srv.cancel(jobs[-1].jid) and srv.cancel(running.jid)
+    assert not srv.cancel(running.jid) and not srv.cancel(12345)
+    srv.tick()                                                # the waiting job takes the lane
+    assert jobs[-2].chain == lane and jobs[-2].phase == "iterate"
+    assert srv.cancel(jobs[-2].jid)                           # give it back once more
+    b = copy.deepcopy(probe)
+    srv.submit(b)
+    _run_until(srv, b)
+    srv.close()
+    assert b.chain == lane
+    assert {j.jid for j in srv.cancelled} == {jobs[-1].jid, running.jid, jobs[-2].jid}
+    assert a.result == b.result, (a.result, b.result)
