@@ -33,6 +33,10 @@ class ea_rt_stats(ctypes.Structure):
                 ("requeue", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+RT_DTYPE = np.dtype([(f, np.int64 if t is ctypes.c_int64 else np.int32) for f, t in ea_rt_stats._fields_])
+assert RT_DTYPE.itemsize == ctypes.sizeof(ea_rt_stats)
+
+
 class ea_chain_desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("L", ctypes.c_int32), ("b_top", ctypes.c_int32),
                 ("parity", ctypes.c_int32), ("rid", ctypes.c_uint32),
@@ -242,10 +246,15 @@ class Context:
         return out
 
     def roundtrips(self, chain0: int = 0, n: int | None = None, reset: bool = False):
+        return [{f: r[f].item() for f in RT_DTYPE.names if f != "pad"}
+                for r in self.roundtrips_array(chain0, n, reset)]
+
+    def roundtrips_array(self, chain0: int = 0, n: int | None = None, reset: bool = False):
+        """Round-trip records as a numpy structured array (fields of ea_rt_stats)."""
         n = self.num_chains() - chain0 if n is None else n
-        out = (ea_rt_stats * n)()
-        check(lib().get_roundtrips(self._h, chain0, n, out, int(reset)))
-        return [{f: getattr(r, f) for f, _ in ea_rt_stats._fields_ if f != "pad"} for r in out]
+        out = np.zeros(n, dtype=RT_DTYPE)
+        check(lib().get_roundtrips(self._h, chain0, n, _p(out), int(reset)))
+        return out
 
     def state(self, chain0: int = 0, n: int | None = None, spins: bool = True):
         n = self.num_chains() - chain0 if n is None else n

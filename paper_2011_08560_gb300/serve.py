@@ -156,10 +156,10 @@ class Server:
                 self.ctx.set_ensemble(j.chain, 1, eamc.EA_POWERLAW, self.alpha, self.pole)
                 self.active[j.chain] = j
 
-    def _finish(self, job: Job, rt: dict, now: float, censored: bool):
-        n = rt["n_rt"]
-        tau = (rt["t_last"] - rt["t_first"]) / n if n > 0 else math.inf
-        job.result = {"n_rt": n, "tau_sweeps": tau, "e_g": rt["e_g"], "e_min": rt["e_min"],
+    def _finish(self, job: Job, rt, now: float, censored: bool):
+        n = int(rt["n_rt"])
+        tau = int(rt["t_last"] - rt["t_first"]) / n if n > 0 else math.inf
+        job.result = {"n_rt": n, "tau_sweeps": tau, "e_g": int(rt["e_g"]), "e_min": int(rt["e_min"]),
                       "sweeps": job.ticks * self.sweeps_per_tick(job.L), "requeues": job.requeues}
         job.phase = "censored" if censored else "done"
         job.t_done = now
@@ -194,7 +194,7 @@ class Server:
         prod = [j for j in jobs if j.phase == "produce"]
         if not prod:
             return
-        rts = self.ctx.roundtrips()
+        rts = self.ctx.roundtrips_array()
         done_now = time.perf_counter()
         for j in prod:
             j.prod_ticks += 1
