@@ -264,9 +264,19 @@ def run_gpu(args, rank, world):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = props.multi_processor_count * 4 * 32 * sm_max * 1e6   # lane-instr/s issue limit
 
-    # end to end through the C ABI with host buffers (weights in, histograms/weights/rt out)
+    # end to end through the C ABI with host buffers in pinned memory (weights in; histograms,
+    # weights and round-trip records out)
+    from paper_2011_08560_gb300.eamc import RT_DTYPE
     rows = max(d["b_top"] for d in ctx.describe()) + 1
-    lnW_host = ctx.get_weights(rows=rows)
+
+    def pinned(shape, dtype):
+        nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
+        return torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy().view(dtype).reshape(shape)
+
+    lnW_host = pinned((n_chains, rows), np.float64)
+    hist = pinned((n_chains, rows), np.uint32)
+    rt = pinned((n_chains,), RT_DTYPE)
+    ctx.get_weights(rows=rows, out=lnW_host)
     e2e_ms = []
     for k in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
@@ -274,13 +284,13 @@ def run_gpu(args, rank, world):
         with torch.cuda.stream(stream):
             ctx.set_weights(0, lnW_host)
             ctx.run_sweeps(S, count_roundtrips=True)
-            hist = ctx.histograms(rows=rows)
+            ctx.histograms(rows=rows, out=hist)
             ctx.update_weights()
-            lnW_host = ctx.get_weights(rows=rows)
-            rt = ctx.roundtrips()
+            ctx.get_weights(rows=rows, out=lnW_host)
+            ctx.roundtrips_array(out=rt)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     h2d = lnW_host.nbytes
-    d2h = hist.nbytes + lnW_host.nbytes + len(rt) * 32
+    d2h = hist.nbytes + lnW_host.nbytes + rt.nbytes
 
     plain = None
     if not args.no_plain and rank == 0:

@@ -124,6 +124,15 @@ def check(rc: int) -> int:
     return rc
 
 
+def _out(out, shape, dtype):
+    """A caller's output buffer after checking it, or a new zeroed one."""
+    if out is None:
+        return np.zeros(shape, dtype=dtype)
+    if out.shape != tuple(shape) or out.dtype != np.dtype(dtype) or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"output buffer must be C-contiguous {np.dtype(dtype)} of shape {tuple(shape)}")
+    return out
+
+
 def _p(a: np.ndarray):
     if a is None:
         return None
@@ -195,10 +204,11 @@ class Context:
         lnW = np.ascontiguousarray(np.atleast_2d(lnW), dtype=np.float64)
         check(lib().muca_set_weights(self._h, chain0, lnW.shape[0], _p(lnW), lnW.shape[1]))
 
-    def get_weights(self, chain0: int = 0, n: int | None = None, rows: int | None = None):
+    def get_weights(self, chain0: int = 0, n: int | None = None, rows: int | None = None, out=None):
+        """ln W rows; `out` (float64 [n, rows], e.g. in pinned memory) is filled when given."""
         n = self.num_chains() - chain0 if n is None else n
         rows = self._rows(chain0, n) if rows is None else rows
-        out = np.zeros((n, rows), dtype=np.float64)
+        out = _out(out, (n, rows), np.float64)
         check(lib().muca_get_weights(self._h, chain0, n, _p(out), rows))
         return out
 
@@ -238,10 +248,10 @@ class Context:
         return out
 
     def histograms(self, chain0: int = 0, n: int | None = None, reset: bool = False,
-                   rows: int | None = None):
+                   rows: int | None = None, out=None):
         n = self.num_chains() - chain0 if n is None else n
         rows = self._rows(chain0, n) if rows is None else rows
-        out = np.zeros((n, rows), dtype=np.uint32)
+        out = _out(out, (n, rows), np.uint32)
         check(lib().get_histograms(self._h, chain0, n, _p(out), rows, int(reset)))
         return out
 
@@ -249,10 +259,10 @@ class Context:
         return [{f: r[f].item() for f in RT_DTYPE.names if f != "pad"}
                 for r in self.roundtrips_array(chain0, n, reset)]
 
-    def roundtrips_array(self, chain0: int = 0, n: int | None = None, reset: bool = False):
+    def roundtrips_array(self, chain0: int = 0, n: int | None = None, reset: bool = False, out=None):
         """Round-trip records as a numpy structured array (fields of ea_rt_stats)."""
         n = self.num_chains() - chain0 if n is None else n
-        out = np.zeros(n, dtype=RT_DTYPE)
+        out = _out(out, (n,), RT_DTYPE)
         check(lib().get_roundtrips(self._h, chain0, n, _p(out), int(reset)))
         return out
 
