@@ -120,3 +120,31 @@ def test_combination_is_the_inverse_variance_mean(orc):
     assert abs(np.var(est) / v_opt - 1.0) < 0.1, (np.var(est), v_opt)
     assert np.var(est) < 0.9 * np.var(est_plain)
     assert abs(np.mean(est) - d_true) < 0.01
+
+
+def test_recovers_from_an_accumulated_trap(orc):
+    """An accumulated estimate that over-weights the ground-state bin (by e^25) traps the chain
+    there: it then visits that bin only, so no pair estimate arrives that could correct D.  The
+    pair the chain stays on one side of must restart from the plain step; the recursion then
+    escapes and converges to the exact density of states."""
+    dim, L, seed, rid = 2, 4, 21, 1
+    J = orc.make_disorder(dim, L, seed, rid)
+    lnO, par, bt = _exact_lnomega_bins(orc, dim, L, J)
+    reach = np.isfinite(lnO)
+    bg = int(np.argmax(reach))
+    lnW = np.where(reach, -(lnO - lnO[bt]), 0.0)
+    lnW[bg] += 25.0
+    acc = orc.berg_state(bt + 1)
+    acc[0, :bt] = lnW[:bt] - lnW[1:]          # D consistent with the trapped weights (flat)
+    acc[1, :bt] = 50.0
+    ch = orc.Chain(dim, L, seed, rid, J=J)
+    e_g = orc.energy_of_bin(dim, L, par, bg)
+    for it in range(12):
+        ch.hist[:] = 0
+        ch.sweeps(5000, orc.quantize(dim, lnW))
+        lnW = orc.update_weights_berg(dim, L, par, 0, -3.6, 8.0, e_g, lnW, ch.hist, acc)
+    ch.hist[:] = 0
+    ch.sweeps(20000, orc.quantize(dim, lnW))
+    assert (ch.hist[reach] > 0).all(), ch.hist        # no longer confined to one bin
+    resid = (lnW + lnO)[reach]
+    assert np.ptp(resid) < 0.3, resid
