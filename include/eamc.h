@@ -175,7 +175,10 @@ int muca_update_weights(ea_ctx *ctx);
  * ln Omega(b+1) - ln Omega(b) with inverse Poisson variance g = H(b)H(b+1)/(H(b)+H(b+1)); the
  * chain keeps D(b) (the g-weighted mean of all its estimates) and G(b) (the sum of the g), and
  * muca_update_weights then sets ln W(b) - ln W(b+1) = ln P_SH(b) - ln P_SH(b+1) + D(b) where
- * G(b) > 0 and the plain step's difference elsewhere, ln W(b_top) = 0.  An iteration run with
+ * G(b) > 0 and the plain step's difference elsewhere, ln W(b_top) = 0.  A pair of which an
+ * iteration visited exactly one bin, although D predicted at least 10 counts on the other
+ * (H(visited) Omega W ratio >= 10), starts over (D = G = 0): weights that confine the chain to
+ * one side of a pair would otherwise never be corrected.  An iteration run with
  * weights that are constant over the range adds no estimates (every move inside the range is
  * then accepted, so the sequential sweep is deterministic).  The first EA_REC_BERG call of a
  * context allocates 16 bytes per bin of every chain and releases a captured graph.

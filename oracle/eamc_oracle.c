@@ -274,10 +274,11 @@ void or_update_weights(int dim, int L, int parity, int b_top, int kind, double a
  *     ln W(b) - ln W(b+1) = ln P_SH(b) - ln P_SH(b+1) + D(b)       (target with the current E_g)
  * for every pair with G(b) > 0; a pair never visited together takes the difference that the
  * plain step (or_update_weights) gives it.  ln W is 0 at the top bin.  From D = G = 0 the
- * first step equals the plain step.  A pair of which the iteration visited exactly one bin
- * restarts (D = G = 0) and takes the plain step: accumulated weights that confine the chain to
- * one side of a pair would otherwise never be corrected (found on ground-state bins, which the
- * chain could not leave once their accumulated weight was too large).
+ * first step equals the plain step.  A pair of which the iteration visited exactly one bin,
+ * although the accumulated estimate expected at least 10 counts on the other side, restarts
+ * (D = G = 0) and takes the plain step: accumulated weights that confine the chain to one side
+ * of a pair would otherwise never be corrected (found on ground-state bins, which the chain
+ * could not leave once their accumulated weight was too large).
  *
  * Weights that are constant over the range add no estimates: every move inside the range is
  * then accepted with probability 1, so the sequential sweep is deterministic (it only flips
@@ -298,12 +299,19 @@ void or_update_weights_berg(int dim, int L, int parity, int b_top, int kind, dou
             double g = h0 * h1 / (h0 + h1);
             D[b] = (G[b] * D[b] + g * s) / (G[b] + g);
             G[b] = G[b] + g;
-        } else if (informative && (hist[b] > 0) != (hist[b + 1] > 0)) {
-            /* the chain stayed on one side of the pair: the weights the accumulated estimate
-             * produced keep it there, and no estimate can arrive to correct them, so the pair
-             * starts over (plain step now, accumulation from the next joint visit) */
-            D[b] = 0.0;
-            G[b] = 0.0;
+        } else if (informative && G[b] > 0.0 && (hist[b] > 0) != (hist[b + 1] > 0)) {
+            /* the chain stayed on one side of the pair.  Under the accumulated estimate the
+             * other side should have collected H(visited) * Omega W ratio counts; if that is at
+             * least 10 (zero of them has probability below 5e-5), the estimate is contradicted
+             * and the weights built from it confine the chain, which no later estimate could
+             * correct: the pair starts over (plain step now, accumulation from the next joint
+             * visit) */
+            double lnexp = (hist[b] > 0) ? (log(h0) + D[b]) + (lnW[b + 1] - lnW[b])
+                                         : (log(h1) - D[b]) + (lnW[b] - lnW[b + 1]);
+            if (lnexp >= 2.302585092994046) {          /* ln 10 */
+                D[b] = 0.0;
+                G[b] = 0.0;
+            }
         }
         if (G[b] > 0.0) {
             diff[b] = lp0 - lp1 + D[b];

@@ -180,7 +180,10 @@ constexpr int kMaxRows = 1297;
 // acc[b] = {D, G} holds the g-weighted mean of all estimates and the sum of the g.  New weights:
 // ln W(b) - ln W(b+1) = ln P_SH(b) - ln P_SH(b+1) + D(b) where G(b) > 0, the plain step's
 // difference elsewhere, ln W(b_top) = 0.  Weights constant over the range add no estimates (the
-// sweep is then deterministic, every move inside the range being accepted).
+// sweep is then deterministic, every move inside the range being accepted).  A pair of which the
+// iteration visited exactly one bin although the accumulated estimate expected at least 10 counts
+// on the other side starts over: weights that confine the chain to one side would otherwise
+// never be corrected.
 __device__ void update_weights_berg(const TileDesc &td, const SlotState &ss, double *__restrict__ w,
                                     const uint32_t *__restrict__ h, double2 *__restrict__ acc, int e_g) {
     __shared__ double diff[kMaxRows];
@@ -200,6 +203,16 @@ __device__ void update_weights_berg(const TileDesc &td, const SlotState &ss, dou
             a.x = __ddiv_rn(__dadd_rn(__dmul_rn(a.y, a.x), __dmul_rn(g, s)), __dadd_rn(a.y, g));
             a.y = __dadd_rn(a.y, g);
             acc[b] = a;
+        } else if (informative && a.y > 0.0 && ((c0 > 0u) != (c1 > 0u))) {
+            // the chain stayed on one side of the pair although the accumulated estimate
+            // expected at least 10 counts on the other: start the pair over (plain step now)
+            const double lnexp = (c0 > 0u)
+                ? __dadd_rn(__dadd_rn(log((double)c0), a.x), __dsub_rn(w[b + 1], w[b]))
+                : __dadd_rn(__dsub_rn(log((double)c1), a.x), __dsub_rn(w[b], w[b + 1]));
+            if (lnexp >= 2.302585092994046) {  // ln 10
+                a = make_double2(0.0, 0.0);
+                acc[b] = a;
+            }
         }
         if (a.y > 0.0) {
             diff[b] = __dadd_rn(__dsub_rn(lp0, lp1), a.x);

@@ -148,3 +148,32 @@ def test_recovers_from_an_accumulated_trap(orc):
     assert (ch.hist[reach] > 0).all(), ch.hist        # no longer confined to one bin
     resid = (lnW + lnO)[reach]
     assert np.ptp(resid) < 0.3, resid
+
+
+@pytest.mark.parametrize("expected,restart", [(3.0, False), (9.5, False), (10.5, True), (300.0, True)])
+def test_one_sided_pair_restarts_only_when_contradicted(orc, expected, restart):
+    """A pair visited on one side only keeps its accumulated estimate while that estimate
+    predicts few counts on the other side (zero of a Poisson mean of 3 has probability e^-3,
+    no evidence against it) and restarts once it predicted at least 10 (probability below
+    5e-5): then the plain step applies and the accumulators are empty."""
+    dim, L, par, bt = 2, 4, 0, 1
+    w0 = np.array([0.5, 0.0])
+    for side in (0, 1):
+        n = 1000
+        hist = np.zeros(2, np.uint32)
+        hist[side] = n
+        # expected count on the empty side: n * exp(+-D + lnW(other) - lnW(side))
+        if side == 0:
+            d = np.log(expected / n) - (w0[1] - w0[0])
+        else:
+            d = -(np.log(expected / n) - (w0[0] - w0[1]))
+        acc = orc.berg_state(2)
+        acc[0, 0], acc[1, 0] = d, 100.0
+        w = orc.update_weights_berg(dim, L, par, 0, 0.0, 1.0, -32, w0, hist, acc)
+        plain = orc.update_weights(dim, L, par, 0, 0.0, 1.0, -32, w0, hist)
+        if restart:
+            assert acc[0, 0] == 0.0 and acc[1, 0] == 0.0
+            np.testing.assert_allclose(w, plain, atol=1e-12)
+        else:
+            assert acc[0, 0] == d and acc[1, 0] == 100.0
+            np.testing.assert_allclose(w[0] - w[1], d, atol=1e-12)     # flat target: diff = D
