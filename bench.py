@@ -66,6 +66,9 @@ def parse():
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--pt-sweeps", type=int, default=200)
+    ap.add_argument("--scan-L", type=int, default=6, help="lattice size of the profile scan")
+    ap.add_argument("--scan-prod-sweeps", type=int, default=100_000,
+                    help="production sweeps of the profile scan")
     return ap.parse_args()
 
 
@@ -606,7 +609,8 @@ def main():
 
     if args.only:
         fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
-              "uneven": bench_uneven, "serving": bench_serving, "scan": bench_profile_scan,
+              "uneven": bench_uneven, "serving": bench_serving,
+              "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "recursion": bench_recursion}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
