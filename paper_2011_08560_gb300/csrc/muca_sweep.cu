@@ -217,11 +217,20 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
             uint4 *buf = hand + k * G::HQ * 32;
             if (warp >= 2) {  // random words: Philox call g covers sites x = 4g .. 4g+3
+                // stored as min(r, 2^32 - 2) (an inactive chain: 2^32 - 1), so that the
+                // consumer's single test r < th is the rule "r < th or th = always" of an
+                // active chain and never accepts for an inactive one; thresholds below
+                // "always" are at most 2^32 - 2, which the clamp does not reach
                 const uint32_t c3 = ss.stream << 8;
 #pragma unroll
-                for (int g = warp - 2; g < G::NG; g += 2)
-                    buf[(G::SUMQ + g) * 32 + lane] =
-                        philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
+                for (int g = warp - 2; g < G::NG; g += 2) {
+                    uint4 w = philox4x32_10(make_uint4((uint32_t)(4 * row + g), tt, ss.rid, c3), key);
+                    w.x = active ? min(w.x, kAlways - 1u) : kAlways;
+                    w.y = active ? min(w.y, kAlways - 1u) : kAlways;
+                    w.z = active ? min(w.z, kAlways - 1u) : kAlways;
+                    w.w = active ? min(w.w, kAlways - 1u) : kAlways;
+                    buf[(G::SUMQ + g) * 32 + lane] = w;
+                }
                 return;
             }
             const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
@@ -423,7 +432,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
                 nB = nB1;
             }
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
-            const bool acc = active && (th == kAlways || r < th);
+            const bool acc = r < th;  // r clamped by the producer (see there)
             accN |= T(acc ? 1u : 0u) << (4 * x);
             resb[x * 32] = acc ? rx + dx : rx;  // row offset after the attempt, for the measurement
             rq = rx;
