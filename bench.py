@@ -49,7 +49,7 @@ LATENCY_FLOOR_CYCLES = 20.0
 PT_ALG_OPS = 4.7
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch of the headline workload
 # (ncu, profiles/muca_sweep_L6_2048chains.md)
-SWEEP_TRAFFIC_BYTES = 11.63e6
+SWEEP_TRAFFIC_BYTES = 11.59e6
 
 
 def parse():
