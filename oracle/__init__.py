@@ -86,7 +86,8 @@ def lib():
             "or_btop": (i32, [i32, i32, i32]),
             "or_descend": (i32, [i32, i32, P, P, i32, P]),
             "or_muca_sweeps": (i32, [i32, i32, u64, u32, u32, P, P, P, u64, u64, P, i32, P,
-                                     P, i32, P]),
+                                     P, i32, P, P]),
+            "or_rt_replay": (None, [P, P, i32, i32, i32, P]),
             "or_quantize": (None, [i32, i32, P, P]),
             "or_ln_profile": (f64, [i32, f64, f64, i32, i32]),
             "or_update_weights": (None, [i32, i32, i32, i32, i32, f64, f64, i32, P, P]),
@@ -97,7 +98,7 @@ def lib():
             "or_pt_colour": (i32, [i32, i32, i32]),
             "or_pt_adapt": (None, [i32, P, P, P, f64]),
             "or_pt_sweeps": (i32, [i32, i32, u64, u32, i32, P, P, P, P, u64, u64, P, P, i32,
-                                   P, i32, i32, i32, P]),
+                                   P, i32, i32, i32, P, P]),
             "or_dos_bruteforce": (i32, [i32, i32, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -213,6 +214,18 @@ def build_weights(dim, L, par, kind, alpha, pole, beta, e_g, lnOmega) -> np.ndar
     return lnW
 
 
+def rt_replay(energies, times, e_top: int, e_bottom: int, rt: RT | None = None) -> RT:
+    """Runs the oracle's round-trip check (Sec. III) once per element of `energies`, observed
+    at sweep indices `times`, starting from `rt` (default: a fresh record, phase 0)."""
+    E = np.ascontiguousarray(energies, dtype=np.int32)
+    t = np.ascontiguousarray(times, dtype=np.int64)
+    assert E.shape == t.shape and E.ndim == 1
+    if rt is None:
+        rt = RT(phase=0, n_rt=0, t_first=-1, t_last=-1, e_min=0, e_g=e_bottom, requeue=0, pad=0)
+    lib().or_rt_replay(_p(E), _p(t), E.shape[0], e_top, e_bottom, ctypes.byref(rt))
+    return rt
+
+
 def dos_bruteforce(dim: int, L: int, J: np.ndarray) -> np.ndarray:
     g = np.zeros(nbonds(dim, L) + 1, dtype=np.uint64)
     if lib().or_dos_bruteforce(dim, L, _p(J), _p(g)) != 0:
@@ -242,18 +255,24 @@ class Chain:
         self.rt = RT(phase=0, n_rt=0, t_first=-1, t_last=-1, e_min=self.E, e_g=-(1 << 30),
                      requeue=0, pad=0)
 
-    def sweeps(self, n: int, thr: np.ndarray, count_rt: bool = False, trace: bool = False):
+    def sweeps(self, n: int, thr: np.ndarray, count_rt: bool = False, trace: bool = False,
+               attempt_trace: bool = False):
+        """n sweeps; returns the energy after each sweep (trace=True), the energy after each
+        attempt as an (n, V) array (attempt_trace=True), both as a tuple, or None."""
         thr = np.ascontiguousarray(thr, dtype=np.uint32)
         assert thr.shape[0] >= (self.b_top + 1) * 8
         E = np.array([self.E], dtype=np.int32)
         tr = np.zeros(n, dtype=np.int32) if trace else None
+        at = np.zeros((n, self.V), dtype=np.int32) if attempt_trace else None
         lib().or_muca_sweeps(self.dim, self.L, self.seed, self.rid, self.stream, _p(self.J),
                              _p(self.S), _p(E), self.t, n, _p(thr), self.b_top, _p(self.hist),
                              ctypes.byref(self.rt), int(count_rt),
-                             _p(tr) if trace else None)
+                             _p(tr) if trace else None, _p(at) if attempt_trace else None)
         self.E = int(E[0])
         self.t += n
-        return tr
+        if trace and attempt_trace:
+            return tr, at
+        return at if attempt_trace else tr
 
 
 # ------------------------------------------------------------------------- PT
@@ -331,11 +350,17 @@ class PTRealization:
         self.set_betas(pt_adapt(self.betas, acc, att, eta))
         self._win_t, self._win_acc = self.t, self.swap_acc.copy()
 
-    def sweeps(self, n: int, count_rt: bool = False, e_g: int = 0, e_hot: int = 0):
+    def sweeps(self, n: int, count_rt: bool = False, e_g: int = 0, e_hot: int = 0,
+               label_trace: bool = False):
+        """n PT sweeps; with label_trace=True returns the (n, M) energies of each replica
+        label after every sweep's exchanges."""
+        lt = np.zeros((n, self.M), dtype=np.int32) if label_trace else None
         rc = lib().or_pt_sweeps(self.dim, self.L, self.seed, self.rid, self.M, _p(self.J),
                                 _p(self.S), _p(self.E), _p(self.label), self.t, n,
                                 _p(self.thr_k), _p(self.thr_pair), self.dmax, self.rt,
-                                int(count_rt), e_g, e_hot, _p(self.swap_acc))
+                                int(count_rt), e_g, e_hot, _p(self.swap_acc),
+                                _p(lt) if label_trace else None)
         if rc != 0:
             raise ValueError("or_pt_sweeps failed")
         self.t += n
+        return lt

@@ -178,16 +178,24 @@ static void rt_check(or_rt *rt, int E, int e_top, int e_bottom, uint64_t t) {
     }
 }
 
+/* The same check applied to a given sequence of energies E[k] observed at sweep indices t[k]
+ * (one check per element, in order): exposes the counter on its own so that it can be pinned
+ * with hand-made sequences. */
+void or_rt_replay(const int32_t *E, const int64_t *t, int n, int e_top, int e_bottom, or_rt *rt) {
+    for (int k = 0; k < n; ++k) rt_check(rt, E[k], e_top, e_bottom, (uint64_t)t[k]);
+}
+
 /* ---------------------------------------------------------------- MUCA chain */
 /* n_sweeps sweeps of single-spin-flip generalized Metropolis (Eq. "muca"), sites in
  * lexicographic order.  thr is the chain's table, thr[b*8 + n] = threshold for a move
  * from bin b at a site with n unsatisfied bonds (the move changes E by 2*(2*dim) - 4n).
- * After every attempt: e_min update and (if count_rt) one round-trip check against
- * rt->e_g.  After every sweep: hist[bin(E)] += 1 and e_trace[s] = E (if non-null). */
+ * After every attempt: e_min update, (if count_rt) one round-trip check against rt->e_g,
+ * and a_trace[s*V + i] = E (if non-null).  After every sweep: hist[bin(E)] += 1 and
+ * e_trace[s] = E (if non-null). */
 int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
                    const int8_t *J, int8_t *S, int32_t *E_io, uint64_t t0, uint64_t n_sweeps,
                    const uint32_t *thr, int b_top, uint32_t *hist, or_rt *rt, int count_rt,
-                   int32_t *e_trace) {
+                   int32_t *e_trace, int32_t *a_trace) {
     int V = or_volume(dim, L), z = 2 * dim;
     int E = *E_io;
     int parity = ((E + or_nbonds(dim, L)) / 2) & 1;
@@ -207,6 +215,7 @@ int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
             if (accept) { S[i] = (int8_t)-S[i]; E += dE; }
             if (E < rt->e_min) rt->e_min = E;
             if (count_rt) rt_check(rt, E, e_top, rt->e_g, t);
+            if (a_trace) a_trace[(size_t)s * V + i] = E;
         }
         hist[or_bin_of_energy(dim, L, E)] += 1;
         if (e_trace) e_trace[s] = E;
@@ -438,11 +447,12 @@ int or_pt_colour(int dim, int L, int i) {
  * Per sweep t: every slot gets a Metropolis sweep colour class by colour class (or_pt_colour;
  * each class in lexicographic order); then exchanges between slots (k, k+1) for
  * k = t mod 2, t mod 2 + 2, ...; then, if count_rt, one round-trip check per replica with
- * bottom e_g and top e_hot (Sec. III). rt is indexed by label. */
+ * bottom e_g and top e_hot (Sec. III). rt is indexed by label.  label_trace (if non-null)
+ * receives, per sweep s, the energy of replica label m at [s*M + m] after the exchanges. */
 int or_pt_sweeps(int dim, int L, uint64_t seed, uint32_t rid, int M, const int8_t *J,
                  int8_t *S, int32_t *E, int32_t *label, uint64_t t0, uint64_t n_sweeps,
                  const uint32_t *thr_k, const uint32_t *thr_pair, int dmax, or_rt *rt,
-                 int count_rt, int e_g, int e_hot, uint64_t *swap_acc) {
+                 int count_rt, int e_g, int e_hot, uint64_t *swap_acc, int32_t *label_trace) {
     int V = or_volume(dim, L), z = 2 * dim;
     int ncol = or_pt_colours(L);
     int8_t *tmp = (int8_t *)malloc((size_t)V);
@@ -490,6 +500,7 @@ int or_pt_sweeps(int dim, int L, uint64_t seed, uint32_t rid, int M, const int8_
             or_rt *r = &rt[label[k]];
             if (E[k] < r->e_min) r->e_min = E[k];
             if (count_rt) rt_check(r, E[k], e_hot, e_g, t);
+            if (label_trace) label_trace[(size_t)s * M + label[k]] = E[k];
         }
     }
     free(tmp);
