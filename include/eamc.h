@@ -336,9 +336,11 @@ int pt_adapt(ea_ctx *ctx, double eta);
  *   thr[c][B][8]               uint32 acceptance thresholds (in), B = (dim*V/2 >> 1) + 1
  *   hist[c][B]                 uint32 histogram (in / out, accumulated)
  * t0 is the sweep index of the first sweep (random words are keyed by it, so two calls with
- * t0 and t0 + n_sweeps continue one trajectory).  Work is queued on cuda_stream (may be NULL)
- * and the call returns after it completes.  EA_EINVAL if a chain starts above E_top (the
- * chain is then left unchanged). */
+ * t0 and t0 + n_sweeps continue one trajectory); t0 + n_sweeps <= 2^32.  As in a context, moves
+ * out of a chain's range [0, b_top] are rejected whatever thr holds there.  Work is queued on
+ * cuda_stream (may be NULL) and the call returns after it completes.  EA_EINVAL if a chain
+ * starts above E_top: the call then runs nothing and writes no output buffer, so it may be
+ * repeated with the same t0 once the input is fixed. */
 int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, const uint32_t *rid,
                             const uint32_t *stream_id, const int8_t *couplings, int8_t *spins,
                             int32_t *energies, const uint32_t *thr, uint32_t *hist, uint64_t t0,

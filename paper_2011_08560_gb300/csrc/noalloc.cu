@@ -17,6 +17,7 @@
 // call, and calls that overlap on the GPU (other streams, other host threads) race on it.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 
@@ -34,7 +35,9 @@ constexpr int kMaxDevices = 64;
 constexpr size_t kPad = 64;                        // threshold elements before / after (zero)
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-unsigned char *g_scratch_dev[kMaxDevices] = {nullptr};
+// device address of g_scratch per device, resolved at the first call on that device; atomic
+// because calls may come from several host threads (they all store the same value)
+std::atomic<unsigned char *> g_scratch_dev[kMaxDevices];
 
 struct Layout {
     size_t tiles, slots, spins, bonds, thr, err, end;
@@ -171,17 +174,19 @@ extern "C" int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, con
                     lay.end, kScratchBytes);
     if (!rid || !stream_id || !couplings || !spins || !energies || !thr || !hist)
         return fail(EA_EINVAL, "null buffer");
-    if (t0 + n_sweeps > (1ull << 32)) return fail(EA_EINVAL, "sweep counter would exceed 2^32");
+    if (t0 > (1ull << 32) || n_sweeps > (1ull << 32) - t0)
+        return fail(EA_EINVAL, "sweep counter would exceed 2^32");
     const size_t smem = sweep_smem_bytes(dim, L);
     int dev = 0;
     NA_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(EA_EINVAL, "device %d out of range", dev);
-    if (!g_scratch_dev[dev]) {  // first call on this device: resolve the array's device address
+    unsigned char *base = g_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!base) {  // first call on this device: resolve the array's device address
         void *p = nullptr;
         NA_CUDA(cudaGetSymbolAddress(&p, g_scratch));
-        g_scratch_dev[dev] = (unsigned char *)p;
+        base = (unsigned char *)p;
+        g_scratch_dev[dev].store(base, std::memory_order_release);
     }
-    unsigned char *base = g_scratch_dev[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
     TileDesc *tiles = (TileDesc *)(base + lay.tiles);
     SlotState *slots = (SlotState *)(base + lay.slots);
@@ -199,6 +204,17 @@ extern "C" int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, con
         pack_kernel<2><<<n_tiles, kTile, 0, st>>>(L, n, rid, stream_id, couplings, spins, thr, t0, tiles, slots,
                                                   d_spins, d_bonds, d_thr, d_err);
     NA_CUDA(cudaGetLastError());
+    // a chain outside its range refuses the whole call before any sweep: no output buffer is
+    // written, so a caller may fix the input and call again with the same t0
+    int herr = 0;
+    NA_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaStreamSynchronize(st));
+    if (herr)
+        return fail(EA_EINVAL, "a chain starts above E_top (outside the MUCA range); nothing was run and no "
+                               "output was written");
+    // the caller's tables get the same walls as tables injected into a context
+    // (muca_set_thresholds): moves out of [0, b_top] are rejected whatever the caller wrote
+    NA_CUDA(launch_enforce_walls(tiles, n_tiles, slots, d_thr + kPad, st));
     NA_CUDA(launch_sweeps(tiles, nullptr, n_tiles, n_tiles, nullptr, dim, smem, slots, d_spins, d_bonds,
                           d_thr + kPad, hist, n_sweeps, key, 0, nullptr, st));
     if (dim == 3)
@@ -206,9 +222,6 @@ extern "C" int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, con
     else
         unpack_kernel<2><<<n, 128, 0, st>>>(L, n, slots, d_spins, spins, energies);
     NA_CUDA(cudaGetLastError());
-    int herr = 0;
-    NA_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
-    if (herr) return fail(EA_EINVAL, "a chain starts above E_top (outside the MUCA range); it was left unchanged");
     return EA_OK;
 }
