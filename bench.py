@@ -1,12 +1,14 @@
-"""Benchmark: batched power-law / flat MUCA on the 3D +-J EA spin glass, one JSON line.
+"""Benchmark: batched power-law MUCA on the 3D +-J EA spin glass, one JSON line.
 
-Workload: L=6, 1024 disorder realizations, each run as a flat-MUCA chain and as a
-power-law-MUCA chain (alpha=-3.6, Delta E=96) -> 2048 chains in one context, packed 32 per
-warp.  One step = one pass of the hot path over the batch: `sweeps_per_step` sweeps of
-generalized Metropolis with histogram, lowest-energy and round-trip measurement
-(muca_run_sweeps), then one weight-iteration update with re-quantisation
-(muca_update_weights).  Metric: spin-flip attempts per ns (whole job), with round trips per
-second beside it.
+Headline workload: L=8, 1024 disorder realizations, each a power-law MUCA chain (alpha=-3.6,
+Delta E=96, Sec. II) packed into multi-spin-coded tiles.  Before timing, the weights iterate
+with Berg's accumulated recursion (the iteration phase, timed and reported on its own); then
+E_g is fixed at each chain's lowest energy, the round-trip records are reset and the weights
+are frozen (Sec. III: round trips are measured with weights determined beforehand).  One step
+= one production pass over the batch: `sweeps_per_step` sweeps of generalized Metropolis with
+histogram, lowest-energy and round-trip measurement (muca_run_sweeps).  Metric: spin-flip
+attempts per ns (whole job), with round trips per second and the mean round-trip time in
+sweeps beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -30,15 +32,16 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-from paper_2011_08560_gb300.workloads import HEADLINE  # noqa: E402
+from paper_2011_08560_gb300.workloads import HEADLINE, L6_FLAT_PL, SMALL  # noqa: E402
 
-METRIC = "spin-flip attempts/ns"
+METRIC = "spin-flip attempts/ns (L=8, power-law ensemble)"
 UNIT = "attempts/ns"
-# algorithmic integer lane-operations per spin-flip attempt:
-# 10 (quarter of a Philox4x32-10 call) + 3.5 (bit-sliced local field, 32 chains per word,
-# plus extraction) + 3 (threshold fetch and compare) + 2 (flip and energy update)
-# + 3 (lowest energy and round-trip check)
-ALG_OPS_PER_ATTEMPT = 21.5
+# algorithmic integer lane-operations per spin-flip attempt, the count of the hot-path scope:
+# 20 (a quarter of a Philox4x32-10 call: 10 rounds of two 32x32->64 products, the xors and the
+# key bumps, about 80 operations for four words) + 10 for the rest (bit-sliced local field of
+# 32 chains per word with extraction 3.5, threshold fetch and compare 3, flip and energy update
+# 2, lowest energy and round-trip check 1.5); the midpoint of the scope's 25-35
+ALG_OPS_PER_ATTEMPT = 30.0
 # per-chain latency floor of one MUCA attempt in SM cycles: with the next attempt's candidate
 # thresholds loaded one attempt ahead, two attempts cost one address select, one shared-memory
 # load (about 29 cycles, measured) and the compare / select of the decision, about 40 cycles
@@ -48,8 +51,8 @@ LATENCY_FLOOR_CYCLES = 20.0
 # 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
 PT_ALG_OPS = 4.7
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch of the headline workload
-# (ncu, profiles/muca_sweep_L6_2048chains.md)
-SWEEP_TRAFFIC_BYTES = 11.59e6
+# from an ncu capture of this kernel version; None until one has been taken
+SWEEP_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -62,10 +65,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
-    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "recursion", "scan"],
+    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "recursion", "scan",
+                                       "small", "flat", "l6"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
-    ap.add_argument("--pt-sweeps", type=int, default=200)
+    ap.add_argument("--iter-steps", type=int, default=None,
+                    help="weight-iteration steps before timing (default: the workload's)")
+    ap.add_argument("--iter-sweeps", type=int, default=None,
+                    help="sweeps per weight-iteration step (default: the workload's)")
+    ap.add_argument("--pt-sweeps", type=int, default=100_000,
+                    help="timed PT sweeps with round-trip counting (the workload names 10^6)")
     ap.add_argument("--scan-L", type=int, default=6, help="lattice size of the profile scan")
     ap.add_argument("--scan-prod-sweeps", type=int, default=100_000,
                     help="production sweeps of the profile scan")
@@ -74,41 +83,51 @@ def parse():
 
 # ------------------------------------------------------------------------------ oracle (CPU)
 def _oracle_worker(args):
+    """One headline chain in the oracle: two short plain iteration steps (untimed) give it
+    power-law-shaped weights, then `sweeps` production sweeps with frozen weights and
+    round-trip counting are timed."""
     import numpy as np
 
     import oracle
     dim, L, seed, rid, stream, kind, sweeps = args
     c = oracle.Chain(dim, L, seed, rid, stream)
     lnW = np.zeros(c.b_top + 1)
+    for _ in range(2):
+        c.sweeps(200, oracle.quantize(dim, lnW))
+        lnW = oracle.update_weights(dim, L, c.parity, kind, HEADLINE.alpha, HEADLINE.pole,
+                                    c.rt.e_min, lnW, c.hist)
+        c.hist[:] = 0
+    c.rt.e_g = c.rt.e_min
+    thr = oracle.quantize(dim, lnW)
     t0 = time.perf_counter()
-    c.sweeps(sweeps, oracle.quantize(dim, lnW), count_rt=True)
-    lnW = oracle.update_weights(dim, L, c.parity, kind, HEADLINE.alpha, HEADLINE.pole,
-                                c.rt.e_min, lnW, c.hist)
+    c.sweeps(sweeps, thr, count_rt=True)
     dt = time.perf_counter() - t0
     return c.V * sweeps, dt, c.rt.n_rt
 
 
 def oracle_sample(target_s: float = 15.0, cores: int | None = None):
-    """Times the oracle on all host cores on a bounded sample of the workload."""
+    """Times the oracle on all host cores on a bounded sample of the headline workload."""
     import oracle
     oracle.build()
     cores = cores or os.cpu_count() or 1
     W = HEADLINE
     # calibrate one chain
-    calib = _oracle_worker((W.dim, W.L, W.seed, 0, 0, 0, 200))
-    per_sweep = calib[1] / 200
+    calib = _oracle_worker((W.dim, W.L, W.seed, 0, 0, 1, 50))
+    per_sweep = calib[1] / 50
     chains = 2 * cores
-    sweeps = max(50, int(target_s * cores / (chains * per_sweep)))
-    jobs = [(W.dim, W.L, W.seed, k // 2, k % 2, k % 2, sweeps) for k in range(chains)]
+    sweeps = max(20, int(target_s * cores / (chains * per_sweep)))
+    jobs = [(W.dim, W.L, W.seed, k, 0, 1, sweeps) for k in range(chains)]
     ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
         res = pool.map(_oracle_worker, jobs)
-    wall = time.perf_counter() - t0
+    # the timed production sweeps of all chains, run side by side on `cores` processes
+    busy = sum(r[1] for r in res)
+    wall = busy / min(cores, chains) if chains else 0.0
     attempts = sum(r[0] for r in res)
     return {"value": attempts / (wall * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{chains} chains (flat and power law alternating) x {sweeps} sweeps + one "
-                      f"weight update each, L={W.L}, {wall:.1f} s wall on {cores} processes",
+            "sample": f"{chains} power-law chains of L={W.L} (realizations 0..{chains - 1}), "
+                      f"{sweeps} production sweeps each with frozen weights and round-trip counting, "
+                      f"{busy:.1f} s of CPU time on {cores} processes",
             "round_trips": sum(r[2] for r in res), "wall_s": wall}
 
 
@@ -178,20 +197,75 @@ def reduce_max_ms(t_ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def build_context(eamc, rank: int, stream_ptr: int):
-    W = HEADLINE
-    ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
+def headline(args):
+    """The headline workload, with the iteration schedule overridden from the command line."""
+    import dataclasses
+    kw = {}
+    if args.iter_steps is not None:
+        kw["iter_steps"] = args.iter_steps
+    if args.iter_sweeps is not None:
+        kw["iter_sweeps"] = args.iter_sweeps
+    return dataclasses.replace(HEADLINE, **kw)
+
+
+def build_context(eamc, rank: int, stream_ptr: int, W=HEADLINE, ensembles=None, tuned=True):
+    """The chains of workload W (one per realization and ensemble, stream = ensemble index),
+    with W's weight recursion and the autotuned tile width and launch; realizations of this
+    rank only."""
+    from paper_2011_08560_gb300 import autotune
+    ens_list = ensembles or W.ensembles
     n = W.n_real
+    best = autotune.tune([(W.dim, W.L, n)] * len(ens_list)) if tuned else None
+    ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
+    if best:
+        autotune.prepare(ctx, best)
     rid0 = shard_rid0(rank, n)
-    ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=0)          # flat MUCA chains
-    ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=1)          # power-law MUCA chains
-    ctx.set_ensemble(0, n, eamc.EA_FLAT)
-    ctx.set_ensemble(n, n, eamc.EA_POWERLAW, W.alpha, W.pole)
+    for s, ens in enumerate(ens_list):
+        first = ctx.init_disorder(W.dim, W.L, n, rid0=rid0, stream=s)
+        kind = eamc.EA_POWERLAW if ens == "powerlaw" else eamc.EA_FLAT
+        ctx.set_ensemble(first, n, kind, W.alpha, W.pole)
+        if W.recursion == "berg":
+            ctx.set_recursion(first, n, eamc.EA_REC_BERG)
+    if best:
+        autotune.launch(ctx, best)
+        ctx.tuned = best
     return ctx
+
+
+def iterate_weights(ctx, W, stream):
+    """The iteration phase (Sec. II): W.iter_steps x (W.iter_sweeps sweeps, then one weight
+    update); then E_g = each chain's lowest energy, and histograms and round-trip records start
+    afresh for production.  Returns (device ms of the sweeps, device ms of the updates)."""
+    import torch
+    sw, up = [], []
+    for _ in range(W.iter_steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ctx.run_sweeps(W.iter_sweeps)
+        e1.record(stream)
+        ctx.update_weights()
+        e2.record(stream)
+        sw.append((e0, e1))
+        up.append((e1, e2))
+    stream.synchronize()
+    ctx.set_eg(0, ctx.num_chains(), None)
+    ctx.roundtrips(reset=True)
+    ctx.histograms(reset=True)
+    return sum(a.elapsed_time(b) for a, b in sw), sum(a.elapsed_time(b) for a, b in up)
 
 
 def total_rt(ctx):
     return sum(r["n_rt"] for r in ctx.roundtrips())
+
+
+def tau_stats(records):
+    """Sec. III: tau_i = (t_last - t_first) / n_rt per chain with a round trip, in sweeps."""
+    taus = [(r["t_last"] - r["t_first"]) / r["n_rt"] for r in records if r["n_rt"] > 0]
+    return {"mean": statistics.mean(taus) if taus else None,
+            "median": statistics.median(taus) if taus else None,
+            "chains_with_round_trip": len(taus), "chains": len(records),
+            "round_trips": sum(r["n_rt"] for r in records),
+            "requeued": sum(1 for r in records if r["requeue"])}
 
 
 def run_gpu(args, rank, world):
@@ -201,29 +275,23 @@ def run_gpu(args, rank, world):
     from paper_2011_08560_gb300 import eamc
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    W = HEADLINE
+    W = headline(args)
     S = args.sweeps_per_step
     stream = torch.cuda.Stream()
-    ctx = build_context(eamc, rank, stream.cuda_stream)
+    ctx = build_context(eamc, rank, stream.cuda_stream, W)
     n_chains = ctx.num_chains()
     V = W.L ** W.dim
     attempts_per_step = n_chains * V * S
+    iter_sweep_ms, iter_update_ms = iterate_weights(ctx, W, stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    def step():
-        ctx.run_sweeps(S, count_roundtrips=True)
-        ctx.update_weights()
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step()
+            ctx.run_sweeps(S, count_roundtrips=True)
     stream.synchronize()
     rt0 = total_rt(ctx)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    # dominant kernel alone: one sweeps launch per step, timed with its own events
-    k_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -233,16 +301,12 @@ def run_gpu(args, rank, world):
             with torch.cuda.stream(stream):
                 flush.fill_(float(k))                       # evict L2 between steps
                 starts[k].record(stream)
-                k_starts[k].record(stream)
-                ctx.run_sweeps(S, count_roundtrips=True)
-                k_ends[k].record(stream)
-                ctx.update_weights()
+                ctx.run_sweeps(S, count_roundtrips=True)    # one launch of the sweep kernel
                 ends[k].record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    kern_ms = [s.elapsed_time(e) for s, e in zip(k_starts, k_ends)]
     t_ms = sum(step_ms)
     if world > 1:
         t_ms = reduce_max_ms(t_ms, world, device="cuda")
@@ -253,22 +317,17 @@ def run_gpu(args, rank, world):
         invariants = "ok"
     except eamc.EamcError as err:
         invariants = str(err)
-    # mean round-trip time in sweeps (Sec. III: tau_i = (t_last - t_first) / n_rt) of the chains
-    # with a round trip so far, by ensemble; the weights iterate once per step meanwhile
-    taus = {"flat": [], "power_law": []}
-    for c, rec in enumerate(ctx.roundtrips()):
-        if rec["n_rt"] > 0:
-            taus["flat" if c < W.n_real else "power_law"].append((rec["t_last"] - rec["t_first"]) / rec["n_rt"])
+    taus = tau_stats(ctx.roundtrips())
     value = world * attempts_per_step * args.steps / (t_ms * 1e6)
-    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    kern_avg_s = statistics.mean(step_ms) / 1e3
     achieved_ops = attempts_per_step * ALG_OPS_PER_ATTEMPT / kern_avg_s
     props = torch.cuda.get_device_properties(0)
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = props.multi_processor_count * 4 * 32 * sm_max * 1e6   # lane-instr/s issue limit
 
-    # end to end through the C ABI with host buffers in pinned memory (weights in; histograms,
-    # weights and round-trip records out)
+    # end to end through the C ABI with host buffers in pinned memory: the frozen weights in,
+    # histograms and round-trip records out, every step
     from paper_2011_08560_gb300.eamc import RT_DTYPE
     rows = max(d["b_top"] for d in ctx.describe()) + 1
 
@@ -288,42 +347,50 @@ def run_gpu(args, rank, world):
             ctx.set_weights(0, lnW_host)
             ctx.run_sweeps(S, count_roundtrips=True)
             ctx.histograms(rows=rows, out=hist)
-            ctx.update_weights()
-            ctx.get_weights(rows=rows, out=lnW_host)
             ctx.roundtrips_array(out=rt)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     h2d = lnW_host.nbytes
-    d2h = hist.nbytes + lnW_host.nbytes + rt.nbytes
+    d2h = hist.nbytes + rt.nbytes
+    ctx.close()
 
     plain = None
     if not args.no_plain and rank == 0:
         plain = plain_form(eamc, stream, S=200)
 
     return {
-        "value": value, "t_ms": t_ms, "step_ms": step_ms, "kern_ms": kern_ms, "wall": wall,
+        "value": value, "t_ms": t_ms, "step_ms": step_ms, "wall": wall,
         "rts": rts, "attempts_per_step": attempts_per_step, "n_chains": n_chains,
         "achieved_ops": achieved_ops, "alu_peak": alu_peak, "clocks": clk.summary(),
         "e2e_ms": statistics.median(e2e_ms), "h2d": h2d, "d2h": d2h, "plain": plain,
         "sm_count": props.multi_processor_count, "taus": taus, "sm_max_mhz": sm_max,
-        "invariants": invariants,
+        "invariants": invariants, "launch": getattr(ctx, "tuned", None),
+        "iteration": {"steps": W.iter_steps, "sweeps_per_step": W.iter_sweeps, "recursion": W.recursion,
+                      "sweep_ms": iter_sweep_ms, "update_ms": iter_update_ms,
+                      "attempts_per_ns": n_chains * V * W.iter_steps * W.iter_sweeps / (iter_sweep_ms * 1e6),
+                      "update_share": iter_update_ms / (iter_sweep_ms + iter_update_ms)},
     }
 
 
+def launches_per_run(launch, sweeps: int) -> int:
+    """Sweep-kernel launches of one muca_run_sweeps call under a launch configuration."""
+    spl = (launch or {}).get("sweeps_per_launch", 0)
+    return 1 if not spl else -(-sweeps // spl)
+
+
 def rt_roofline(r, world):
-    all_taus = r["taus"]["flat"] + r["taus"]["power_law"]
-    if not all_taus:
+    tau = r["taus"]["mean"]
+    if not tau:
         return None
     V = HEADLINE.L ** HEADLINE.dim
-    peak = world * r["alu_peak"] / ALG_OPS_PER_ATTEMPT / (V * statistics.mean(all_taus))
+    peak = world * r["alu_peak"] / ALG_OPS_PER_ATTEMPT / (V * tau)
     achieved = world * r["rts"] / (r["t_ms"] / 1e3)
     return {"achieved": achieved, "peak": peak, "unit": "round trips/s", "frac": achieved / peak,
             "basis": "ALU peak / ops per attempt / (V x mean round-trip time in sweeps)"}
 
 
-def plain_form(eamc, stream, S: int):
+def plain_form(eamc, stream, S: int, W=HEADLINE):
     """One realization per launch: the same kernel with a single chain in the context."""
     import torch
-    W = HEADLINE
     ctx = eamc.Context(seed=W.seed, device=0, stream=stream.cuda_stream)
     ctx.init_disorder(W.dim, W.L, 1, rid0=0)
     ctx.set_ensemble(0, 1, eamc.EA_POWERLAW, W.alpha, W.pole)
@@ -339,11 +406,134 @@ def plain_form(eamc, stream, S: int):
     ms = e0.elapsed_time(e1)
     ctx.close()
     return {"value": W.L ** W.dim * S / (ms * 1e6), "unit": UNIT,
-            "what": f"one realization per launch, {S} sweeps, L={W.L}"}
+            "what": f"one realization per launch, {S} sweeps, L={W.L}, power law"}
 
 
-def bench_pt(S: int = 200):
-    """PT workload: L=8, 1024 realizations x 32 temperatures (geometric beta in [0.2, 3])."""
+def bench_flat_same_schedule(S: int = 10_000, steps: int = 10):
+    """The headline's realizations as flat-MUCA chains under the same schedule (Berg iteration,
+    frozen weights, E_g fixed), for the paper's comparison of round-trip times (Table I)."""
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    W = HEADLINE
+    stream = torch.cuda.Stream()
+    ctx = build_context(eamc, 0, stream.cuda_stream, ensembles=("flat",))
+    iterate_weights(ctx, W, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.run_sweeps(S, count_roundtrips=True)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    recs = ctx.roundtrips()
+    ctx.close()
+    st = tau_stats(recs)
+    return {"workload": f"3D L={W.L}, {W.n_real} realizations, flat MUCA, Berg iteration "
+                        f"{W.iter_steps} x {W.iter_sweeps}, {steps} x {S} production sweeps",
+            "attempts_per_ns": W.n_real * W.L ** 3 * S * steps / (ms * 1e6),
+            "round_trips_per_s": st["round_trips"] / (ms / 1e3), "round_trip_time_sweeps": st}
+
+
+def bench_l6_flat_pl(S: int = 10_000, steps: int = 5):
+    """L=6, 1024 realizations x {flat, power law} = 2048 chains; a step is S sweeps with
+    measurement plus one weight update (plain recursion)."""
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    W = L6_FLAT_PL
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=W.seed, device=0, stream=stream.cuda_stream)
+    ctx.init_disorder(W.dim, W.L, W.n_real, rid0=0, stream=0)
+    ctx.init_disorder(W.dim, W.L, W.n_real, rid0=0, stream=1)
+    ctx.set_ensemble(0, W.n_real, eamc.EA_FLAT)
+    ctx.set_ensemble(W.n_real, W.n_real, eamc.EA_POWERLAW, W.alpha, W.pole)
+    for _ in range(2):
+        ctx.run_sweeps(S, count_roundtrips=True)
+        ctx.update_weights()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.run_sweeps(S, count_roundtrips=True)
+        ctx.update_weights()
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"workload": W.name, "chains": 2 * W.n_real, "steps": steps,
+            "attempts_per_ns": 2 * W.n_real * W.L ** 3 * S * steps / (ms * 1e6)}
+
+
+def _small_oracle_full():
+    """Config 1 in the oracle, in full: the same schedule as bench_small."""
+    import numpy as np
+
+    import oracle
+    W = SMALL
+    c = oracle.Chain(W.dim, W.L, W.seed, 0, 0)
+    lnW = np.zeros(c.b_top + 1)
+    t0 = time.perf_counter()
+    for _ in range(W.iter_steps):
+        c.sweeps(W.iter_sweeps, oracle.quantize(W.dim, lnW))
+        lnW = oracle.update_weights(W.dim, W.L, c.parity, oracle.FLAT, 0.0, 0.0, c.rt.e_min, lnW, c.hist)
+        c.hist[:] = 0
+    c.rt.e_g = c.rt.e_min
+    t1 = time.perf_counter()
+    c.sweeps(W.prod_sweeps, oracle.quantize(W.dim, lnW), count_rt=True)
+    t2 = time.perf_counter()
+    return {"seconds": t2 - t0, "production_seconds": t2 - t1, "n_rt": c.rt.n_rt,
+            "t_first": c.rt.t_first, "t_last": c.rt.t_last, "E": c.E, "e_g": c.rt.e_g}
+
+
+def bench_small():
+    """Config 1: L=4, one realization, flat MUCA, 20 x 10^4 iteration sweeps then 10^5
+    production sweeps, on the GPU and (in full, one core) in the oracle; same trajectory."""
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    W = SMALL
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=W.seed, device=0, stream=stream.cuda_stream)
+    ctx.init_disorder(W.dim, W.L, 1, rid0=0, stream=0)
+    ctx.set_ensemble(0, 1, eamc.EA_FLAT)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(W.iter_steps):
+        ctx.run_sweeps(W.iter_sweeps)
+        ctx.update_weights()
+    e1.record(stream)
+    stream.synchronize()
+    ctx.set_eg(0, 1, None)
+    ctx.roundtrips(reset=True)
+    e1.record(stream)
+    ctx.run_sweeps(W.prod_sweeps, count_roundtrips=True)
+    e2.record(stream)
+    stream.synchronize()
+    it_ms, prod_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    rec = ctx.roundtrips()[0]
+    _, E, _ = ctx.state(spins=False)
+    ctx.close()
+    orc = _small_oracle_full()
+    same = (rec["n_rt"], rec["t_first"], rec["t_last"], int(E[0]), rec["e_g"]) == \
+        (orc["n_rt"], orc["t_first"], orc["t_last"], orc["E"], orc["e_g"])
+    V = W.L ** W.dim
+    total = V * (W.iter_steps * W.iter_sweeps + W.prod_sweeps)
+    return {"workload": W.name, "gpu_ms": it_ms + prod_ms,
+            "gpu_attempts_per_ns": total / ((it_ms + prod_ms) * 1e6),
+            "gpu_production_round_trips_per_s": rec["n_rt"] / (prod_ms / 1e3),
+            "round_trips": rec["n_rt"], "tau_sweeps": (rec["t_last"] - rec["t_first"]) / rec["n_rt"] if rec["n_rt"] else None,
+            "oracle_seconds_one_core": orc["seconds"], "oracle_attempts_per_ns": total / (orc["seconds"] * 1e9),
+            "oracle_production_round_trips_per_s": orc["n_rt"] / orc["production_seconds"],
+            "same_trajectory_as_oracle": same}
+
+
+def bench_pt(S: int = 100_000, equil: int = 10_000, sample_every: int = 100):
+    """Config 3, PT: L=8, 1024 realizations x 32 temperatures (geometric beta in [0.2, 3]);
+    `equil` sweeps of equilibration, in which E_g = the lowest energy any replica of a
+    realization reached and E_hot = the mean energy at the hottest slot (sampled every
+    `sample_every` sweeps of the second half); then S timed sweeps with round trips counted per
+    replica (Sec. III, PT variant)."""
+    import numpy as np
     import torch
 
     from paper_2011_08560_gb300 import eamc
@@ -352,21 +542,40 @@ def bench_pt(S: int = 200):
     ctx = eamc.Context(seed=PT["seed"], device=0, stream=stream.cuda_stream)
     betas = geometric_betas(PT["M"], PT["beta_min"], PT["beta_max"])
     ctx.pt_init(PT["dim"], PT["L"], PT["n_real"], betas)
-    ctx.pt_run(20)
-    stream.synchronize()
+    ctx.pt_run(equil // 2)
+    hot = []
+    for _ in range(equil // 2 // sample_every):
+        ctx.pt_run(sample_every)
+        _, E, _, _ = ctx.pt_state(spins=False)
+        hot.append(E[:, 0].astype(np.int64))
+    e_hot = np.floor(np.mean(hot, axis=0)).astype(np.int32)
+    recs = ctx.pt_roundtrips(reset=True)
+    e_g = np.array([min(r["e_min"] for r in rr) for rr in recs], dtype=np.int32)
+    ctx.pt_set_rt_bounds(e_g, e_hot)
+    sw0 = ctx.pt_swap_counts()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx.pt_run(S)
+    ctx.pt_run(S, count_roundtrips=True)
     e1.record(stream)
     stream.synchronize()
     ms = e0.elapsed_time(e1)
     attempts = PT["n_real"] * PT["M"] * PT["L"] ** 3 * S
-    swaps = ctx.pt_swap_counts()
+    swaps = ctx.pt_swap_counts() - sw0
+    recs = ctx.pt_roundtrips()
     ctx.close()
-    return {"workload": "PT: 3D L=8, 1024 realizations x 32 temperatures, beta geometric in [0.2, 3]",
+    flat = [r for rr in recs for r in rr]
+    taus = [(r["t_last"] - r["t_first"]) / r["n_rt"] for r in flat if r["n_rt"] > 0]
+    n_rt = sum(r["n_rt"] for r in flat)
+    return {"workload": "PT: 3D L=8, 1024 realizations x 32 temperatures, beta geometric in [0.2, 3], "
+                        f"{equil} equilibration + {S} timed sweeps with round trips per replica",
             "sweeps": S, "ms": ms, "attempts_per_ns": attempts / (ms * 1e6),
             "alg_ops_per_attempt": PT_ALG_OPS, "achieved_Tops": attempts * PT_ALG_OPS / (ms * 1e9),
-            "swap_acceptance_mean": float(swaps.sum() / max(1, (PT["M"] - 1) * PT["n_real"] * (20 + S) / 2))}
+            "round_trips_per_s": n_rt / (ms / 1e3), "round_trips": n_rt,
+            "round_trip_time_sweeps": {"mean": statistics.mean(taus) if taus else None,
+                                       "median": statistics.median(taus) if taus else None,
+                                       "replicas_with_round_trip": len(taus), "replicas": len(flat)},
+            "e_hot_mean": float(e_hot.mean()), "e_g_mean": float(e_g.mean()),
+            "swap_acceptance_mean": float(swaps.sum() / max(1, (PT["M"] - 1) * PT["n_real"] * S / 2))}
 
 
 def bench_pt_protocol(rounds: int = 12, window: int = 1000, S: int = 4000):
@@ -439,15 +648,17 @@ def build_uneven(eamc, autotune, stream_ptr, S: int):
     """The uneven batch as the bench runs it: chains, autotuned launch, one iteration step, then
     the 1/k chains take 1/k weights built from their estimate."""
     from paper_2011_08560_gb300.workloads import UNEVEN
+    groups = [(3, L, n) for _, L, _, n in uneven_groups()]
+    best = autotune.tune(groups, sweeps=20)
     ctx = eamc.Context(seed=UNEVEN["seed"], device=0, stream=stream_ptr)
-    groups, one_over_k = [], []
+    autotune.prepare(ctx, best)
+    one_over_k = []
     for kind_idx, L, rid0, n in uneven_groups():
         first = ctx.init_disorder(3, L, n, rid0=rid0, stream=kind_idx)
         ctx.set_ensemble(first, n, eamc.EA_POWERLAW if kind_idx == 0 else eamc.EA_FLAT)
         if kind_idx == 2:
             one_over_k.append((first, n))
-        groups.append((3, L, n))
-    best = autotune.apply(ctx, groups, sweeps=20)
+    autotune.launch(ctx, best)
     ctx.run_sweeps(S, count_roundtrips=False)
     ctx.update_weights()
     for first, n in one_over_k:
@@ -530,14 +741,28 @@ def bench_recursion(L: int = 8, n: int = 256, iters: int = 24, S: int = 2000, P:
     return out
 
 
+# the paper's number of PT replicas per lattice size (Sec. II, PT)
+PT_REPLICAS = {3: 7, 4: 7, 5: 12, 6: 14, 8: 20}
+# the paper's Table I: (r_pop, r_eps) of flat MUCA, the 1/k ensemble and PT relative to PL
+PAPER_TABLE_ONE = {3: {"flat": (1.160, 1.174), "1/k": (1.0146, 1.0193), "PT": (1.637, 1.640)},
+                   4: {"flat": (1.622, 1.68), "1/k": (1.288, 1.328), "PT": (1.175, 1.25)},
+                   5: {"flat": (2.28, 2.44), "1/k": (1.63, 1.75), "PT": (1.136, 1.185)},
+                   6: {"flat": (3.8, 3.9), "1/k": (2.59, 2.6), "PT": (2.8, 3.4)},
+                   8: {"flat": (10.5, 14.2), "1/k": (6.9, 9.4), "PT": (2.1, 2.62)}}
+
+
 def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_sweeps: int = 10000,
-                       prod_sweeps: int = 100000):
+                       prod_sweeps: int = 100000, pt: bool = True):
     """Profile-parameter scan (Sec. II): power-law alpha x Delta E grid, flat and 1/k beside
     it, n_real realizations of L^3, density of states once per realization (power-law target,
-    Berg's recursion), production with round-trip counting in one batched launch.  Reports the
-    mean round-trip time per ensemble and its ratio to flat (jackknife over realizations)."""
+    Berg's recursion), production with round-trip counting in one batched launch; PT with the
+    paper's replica count on the same realizations.  Reports the mean round-trip time per
+    ensemble, its ratio to flat, and the Table I analog: r_pop and r_eps (eps = 1e-4) of flat,
+    1/k and PT relative to the power law (-3.6, 96), with jackknife errors, beside the paper's
+    values (other disorder sets: context, not a target)."""
     import time
 
+    import numpy as np
     import torch
 
     from paper_2011_08560_gb300 import eamc, scan
@@ -548,28 +773,46 @@ def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_
                             dos_sweeps=dos_sweeps, prod_sweeps=prod_sweeps,
                             recursion=eamc.EA_REC_BERG, stream=stream.cuda_stream)
     wall = time.perf_counter() - t0
+    pt_tau = pt_below = None
+    M = PT_REPLICAS.get(L)
+    if pt and M:
+        pt_tau, pt_below = scan.pt_round_trips(3, L, n_real, M, res.e_g, seed=6, prod_sweeps=prod_sweeps,
+                                               stream=stream.cuda_stream)
+    wall_pt = time.perf_counter() - t0 - wall
     rows = res.summary()
-    return {"workload": f"3D L={L}, {n_real} realizations (seed 6), power law alpha in {list(alphas)} x "
-                        f"Delta E in {list(poles)}, flat and 1/k; density of states {dos_iters} x "
-                        f"{dos_sweeps} sweeps (Berg), {prod_sweeps} production sweeps",
-            "wall_s": wall, "best_power_law": res.best(),
-            "ensembles": {r["ensemble"]: {k: v for k, v in r.items() if k != "ensemble"} for r in rows}}
+    out = {"workload": f"3D L={L}, {n_real} realizations (seed 6), power law alpha in {list(alphas)} x "
+                       f"Delta E in {list(poles)}, flat and 1/k; density of states {dos_iters} x "
+                       f"{dos_sweeps} sweeps (Berg), {prod_sweeps} production sweeps; PT with M = {M} "
+                       f"replicas, beta in [0.3, 2.15] adapted over 8 x 1000 sweeps, {prod_sweeps} sweeps",
+           "wall_s": wall, "pt_wall_s": wall_pt, "best_power_law": res.best(),
+           "ensembles": {r["ensemble"]: {k: v for k, v in r.items() if k != "ensemble"} for r in rows},
+           "table_one": res.table_one(pt_tau, pt_below),
+           "paper_table_one": PAPER_TABLE_ONE.get(L)}
+    if pt_tau is not None:
+        ok = np.isfinite(pt_tau)
+        out["pt"] = {"mean_tau": float(np.mean(pt_tau[ok])) if ok.any() else None,
+                     "without_rt": int((~ok).sum()), "below_eg": int(pt_below.sum())}
+    return out
 
 
-def bench_serving(window_s: float = 4.0, drain_s: float = 20.0):
-    """Serving: Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12}, round-trip
-    targets log-uniform in [10, 1000]; device-resident state, memory-based admission."""
+def bench_serving(window_s: float = 10.0, drain_s: float = 30.0):
+    """Serving (config 5): Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12},
+    round-trip targets log-uniform in [10, 1000]; power-law MUCA with Berg's recursion; state
+    resident on the device, admission by memory, job control on the device, asynchronous
+    read-back.  Latency percentiles cover every job: censored jobs count at their cap."""
     from paper_2011_08560_gb300 import serve
     from paper_2011_08560_gb300.workloads import SERVING
     jobs = serve.poisson_jobs(SERVING["rate_hz"], window_s, SERVING["Ls"], SERVING["rt_min"],
-                              SERVING["rt_max"], seed=SERVING["seed"], iter_steps=4,
-                              ticks_per_step=4, max_prod_ticks=200)
-    server = serve.Server(seed=SERVING["seed"], Ls=SERVING["Ls"], base_sweeps=16,
-                          mem_budget=4 << 30)
+                              SERVING["rt_max"], seed=SERVING["seed"], iter_steps=8, ticks_per_step=8,
+                              max_prod_ticks=2000, max_requeues=4)
+    server = serve.Server(seed=SERVING["seed"], Ls=SERVING["Ls"], base_sweeps=16, mem_budget=8 << 30,
+                          poll_ticks=8, max_ahead=64)
     stats = serve.run_poisson(server, jobs, duration_s=window_s, drain_s=drain_s)
     server.close()
     stats["workload"] = (f"Poisson {SERVING['rate_hz']:.0f} jobs/s for {window_s:.0f} s, L in 4..12, "
-                         f"round-trip targets log-uniform [10, 1000], sweep caps (censored jobs counted)")
+                         f"round-trip targets log-uniform [10, 1000], power law + Berg, 8 x 8 iteration "
+                         f"ticks, production cap 2000 ticks (16 sweeps per tick at L=12, (12/L)^3 times "
+                         f"more at smaller L)")
     return stats
 
 
@@ -577,11 +820,13 @@ def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
-    W = HEADLINE
+    W = headline(args)
     config = {"workload": W.name, "L": W.L, "realizations_per_gpu": W.n_real,
-              "chains_per_gpu": 2 * W.n_real, "ensembles": ["flat", "power-law(alpha=-3.6, dE=96)"],
+              "chains_per_gpu": W.n_real, "ensembles": [f"power-law(alpha={W.alpha:g}, dE={W.pole:g})"],
               "sweeps_per_step": args.sweeps_per_step,
-              "step": "sweeps with measurement + one weight-iteration update",
+              "weight_iteration": f"{W.iter_steps} x {W.iter_sweeps} sweeps, {W.recursion} recursion, "
+                                  f"before timing; then E_g fixed, weights frozen",
+              "step": "production sweeps with histogram, lowest-energy and round-trip measurement",
               "l2": "flushed between steps (256 MB write)",
               "parallelism": f"independent realizations, {world} GPU(s)"}
 
@@ -611,7 +856,8 @@ def main():
         fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
               "uneven": bench_uneven, "serving": bench_serving,
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
-              "recursion": bench_recursion}
+              "recursion": bench_recursion, "small": bench_small, "flat": bench_flat_same_schedule,
+              "l6": bench_l6_flat_pl}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
     if world > 1:
@@ -623,51 +869,57 @@ def main():
     r = run_gpu(args, rank, world)
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = {"pt": bench_pt(), "pt_protocol": bench_pt_protocol(), "uneven": bench_uneven(),
-                  "serving": bench_serving(), "recursion": bench_recursion(), "scan": bench_profile_scan()}
+        extras = {"flat_same_schedule": bench_flat_same_schedule(), "l6_flat_pl": bench_l6_flat_pl(),
+                  "small": bench_small(), "pt": bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol(),
+                  "uneven": bench_uneven(), "serving": bench_serving(), "recursion": bench_recursion(),
+                  "scan": bench_profile_scan()}
     if rank != 0:
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()
         return
     attempts_e2e = r["attempts_per_step"] * world
+    lat_peak = world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / LATENCY_FLOOR_CYCLES
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["t_ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded +-J disorder, random initial spins)", "config": config,
         "round_trips_per_s": world * r["rts"] / (r["t_ms"] / 1e3),
+        # Sec. III: tau_i = (t_last - t_first) / n_rt over the production sweeps (warm-up + timed)
+        "round_trip_time_sweeps": r["taus"],
         "invariant_check": r["invariants"],
-        "round_trip_time_sweeps": {
-            k: {"mean": statistics.mean(v) if v else None, "chains_with_round_trip": len(v)}
-            for k, v in r["taus"].items()},
+        "iteration_phase": r["iteration"],
         # round trips/s against the ALU roofline: attempts/s at the roofline / (V x mean tau)
         "round_trips_roofline": rt_roofline(r, world),
         # the bound that applies to a batch of serial chains: every chain needs at least
         # LATENCY_FLOOR_CYCLES per attempt (select + shared-memory load + compare, loads issued
         # one attempt ahead), so attempts/ns <= chains x SM clock / floor
-        "latency_roofline": {"achieved": r["value"],
-                             "peak": world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / LATENCY_FLOOR_CYCLES,
-                             "unit": UNIT,
-                             "frac": r["value"] / (world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / LATENCY_FLOOR_CYCLES),
+        "latency_roofline": {"achieved": r["value"], "peak": lat_peak, "unit": UNIT,
+                             "frac": r["value"] / lat_peak,
                              "cycles_per_attempt_floor": LATENCY_FLOOR_CYCLES,
                              "cycles_per_attempt_achieved": world * r["n_chains"] * r["sm_max_mhz"] * 1e-3 / r["value"]},
         "plain_form": r["plain"],
         "e2e": {"value": attempts_e2e / (r["e2e_ms"] * 1e6), "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": args.steps * launches_per_run(r["launch"], args.sweeps_per_step),
+        "launch": r["launch"],
         "roofline": {"bound": "alu", "achieved": r["achieved_ops"] / 1e12,
                      "peak": r["alu_peak"] / 1e12, "unit": "Tops/s",
                      "frac": r["achieved_ops"] / r["alu_peak"], "traffic": SWEEP_TRAFFIC_BYTES,
-                     "traffic_source": "profiles/muca_sweep_L6_2048chains.md (dram read+write of one "
-                                       "launch; one-time staging of the tables, independent of sweeps)",
                      "kernel": "muca_sweep_kernel<3>",
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
-                     "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock"},
+                     "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock "
+                                   f"(MEASURED_PEAKS.json sm_max_mhz)"},
         "clocks": r["clocks"],
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "extras": extras,
     }
+    if extras and extras.get("pt"):
+        pt = extras["pt"]
+        line["pt_roofline"] = {"bound": "alu", "achieved": pt["achieved_Tops"], "peak": r["alu_peak"] / 1e12,
+                               "unit": "Tops/s", "frac": pt["achieved_Tops"] * 1e12 / r["alu_peak"],
+                               "kernel": "pt_kernel", "ops_per_attempt": PT_ALG_OPS}
     print(json.dumps(line))
     if world > 1:
         import torch

@@ -137,12 +137,26 @@ int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g);
  * t + n_sweeps <= 2^32 for every chain.  Asynchronous on the context stream. */
 int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
 
-/* a8 -- launch configuration of muca_run_sweeps.  persistent = 0: one thread block (two
- * warps) per tile of 32 chains; persistent = 1: a grid of blocks_per_sm blocks per SM (0 = as
+/* a8 -- launch configuration of muca_run_sweeps.  persistent = 0: one thread block per tile;
+ * persistent = 1: a grid of blocks_per_sm blocks per SM (0 = as
  * many as fit) whose blocks pull tiles from a work queue, longest lattices first (for batches
  * of uneven L).  sweeps_per_launch > 0 splits a run into launches of at most that many
  * sweeps (0 = one launch).  Results do not depend on any of these settings. */
 int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch, int blocks_per_sm);
+
+/* a8 -- chains per tile for chains of linear size L added afterwards (ea_init_disorder):
+ * width 32 (the default, every L) or 16 (3D, L = 7, 8).  A tile is one
+ * warp; with width W < 32 each of its W chains runs on 32/W lanes side by side, so the tile needs
+ * W/32 of the shared memory of a full one and these sizes keep their acceptance thresholds in
+ * shared memory instead of reading them through L1: each chain runs faster, the SM holds fewer
+ * chains.  Narrow tiles suit batches with fewer chains than the GPU can hold; results do not
+ * depend on the width.  EA_EINVAL for a width not available at this L. */
+int muca_set_tile_width(ea_ctx *ctx, int L, int width);
+
+/* Properties of the sweep kernel for tiles of (dim, L, width): dynamic shared memory per block
+ * (*smem_bytes, may be NULL) and whether the thresholds live in shared memory
+ * (*thresholds_in_smem, may be NULL).  EA_EINVAL for a width not available at this L. */
+int muca_get_tile_width(int dim, int L, int width, size_t *smem_bytes, int *thresholds_in_smem);
 
 /* a8 / a9 -- every tile of linear size L runs multiplier x the requested sweeps in each
  * muca_run_sweeps call (default 1), so a launch over tiles of uneven L can give small lattices
@@ -315,6 +329,103 @@ int pt_set_betas(ea_ctx *ctx, const double *betas);
 int pt_get_betas(ea_ctx *ctx, double *betas);
 int pt_get_exchange_counts(ea_ctx *ctx, uint32_t *accepted, uint64_t *attempted);
 int pt_adapt(ea_ctx *ctx, double eta);
+
+/* ------------------------------------------------------------------ serving
+ * a9 -- continuous batching of realization jobs (Sec. II ensembles, Sec. III round trips and
+ * requeue).  A server owns one context whose tiles form a pool of lanes per lattice size; jobs
+ * are admitted into free lanes (the pool of an L grows while the memory budget allows: admission
+ * by memory), and all jobs advance together, one tick after another: a sweep launch over every
+ * tile, then per-slot job control on the device (weight steps at each job's step boundaries,
+ * the switch to production, requeue, completion).  The host never waits for a tick: finished
+ * jobs are read back asynchronously every poll_ticks ticks.  A job's schedule is counted in its
+ * own ticks and its random numbers are keyed by its own sweep counter, so its result is the same
+ * alone and among other jobs.  A server is not thread-safe. */
+typedef struct ea_srv ea_srv;
+
+typedef struct {
+    int32_t dim;             /* 3 (2 for small test lattices) */
+    int32_t n_L, Ls[16];     /* lattice sizes served, 3 <= L <= 12 */
+    size_t mem_budget;       /* device bytes the lane pool may take */
+    int32_t base_sweeps;     /* sweeps per tick at the largest L; a lattice of size L gets
+                              * base_sweeps * round((L_max / L)^3), about equal work per tick */
+    int32_t poll_ticks;      /* ticks between completion read-backs */
+    int32_t max_ahead;       /* ticks queued at most beyond the last completed read-back */
+} ea_srv_config;
+
+/* One job: realization rid (couplings and initial spins drawn from the server's seed, as
+ * ea_init_disorder), random stream, ensemble kind EA_FLAT or EA_POWERLAW (alpha, pole), weight
+ * recursion EA_REC_PLAIN or EA_REC_BERG.  Schedule in the job's own ticks: iter_steps weight
+ * steps, one every ticks_per_step ticks; then E_g = the lowest energy seen and production until
+ * rt_target round trips (status EA_JOB_DONE) or max_prod_ticks production ticks (EA_JOB_CENSORED);
+ * a chain that goes below E_g in production is requeued (new E_g, one more weight step,
+ * counting restarts) at most max_requeues times. */
+typedef struct {
+    int32_t L;
+    uint32_t rid, stream;
+    int32_t kind, recursion;
+    double alpha, pole;
+    int32_t rt_target, iter_steps, ticks_per_step, max_prod_ticks, max_requeues, pad;
+} ea_job;
+
+#define EA_JOB_DONE 1
+#define EA_JOB_CENSORED 2
+#define EA_JOB_FAILED 3  /* the chain's descent to E <= E_top got stuck at admission */
+
+/* A finished job: round-trip record of its production (t_first / t_last are sweep indices of
+ * the job's own chain, tau = (t_last - t_first) / n_rt), requeues taken, E_g and the lowest
+ * energy, sweeps done, and host times in seconds since the server was created: submission,
+ * admission into a lane, and the read-back that reported it. */
+typedef struct {
+    uint64_t job_id;
+    int32_t status, L;
+    uint32_t rid;
+    int32_t rt_target, n_rt, requeues;
+    int64_t t_first, t_last;
+    int32_t e_g, e_min;
+    uint64_t sweeps;
+    double t_submit, t_admit, t_done;
+} ea_srv_result;
+
+typedef struct {
+    uint64_t ticks, ticks_read;       /* ticks queued / covered by the last read-back */
+    uint64_t attempts;                /* spin-flip attempts of job lanes (at the last read-back) */
+    int32_t queued, running, lanes, pad;
+    uint64_t done, censored, failed, cancelled, round_trips;
+    size_t mem_used;
+    double seconds;                   /* since the server was created */
+} ea_srv_counters;
+
+/* Creates a server on CUDA device `device`, queuing all work on cuda_stream (not the legacy
+ * default stream if other work shares the device).  EA_EINVAL for a bad configuration. */
+int ea_srv_create(ea_srv **out, int device, void *cuda_stream, uint64_t seed, const ea_srv_config *cfg);
+void ea_srv_destroy(ea_srv *srv);
+
+/* Queues a job (admitted at the next ea_srv_step); *job_id (may be NULL) receives its id.
+ * EA_EINVAL for an L not served, a bad kind / recursion / schedule, or a schedule whose sweeps
+ * would exceed 2^32. */
+int ea_srv_submit(ea_srv *srv, const ea_job *job, uint64_t *job_id);
+
+/* Withdraws a waiting or running job (a running job's lane stops before the next tick and is
+ * reused); EA_ESTATE if the job is neither (unknown or already finished). */
+int ea_srv_cancel(ea_srv *srv, uint64_t job_id);
+
+/* Admits waiting jobs into free lanes (growing the pool within the budget), then queues `ticks`
+ * ticks (none while no job runs).  Returns without waiting for the GPU, except to keep at most
+ * max_ahead ticks in flight. */
+int ea_srv_step(ea_srv *srv, int ticks);
+
+/* Copies up to cap finished jobs into out (host buffer) and their count into *n_out.  wait = 0
+ * only looks at read-backs that have completed; wait != 0 first reads back everything queued. */
+int ea_srv_poll(ea_srv *srv, ea_srv_result *out, int cap, int *n_out, int wait);
+
+int ea_srv_stats(ea_srv *srv, ea_srv_counters *out);
+
+/* Device bytes one tile of 32 lanes of size L takes from a server's memory budget (0 for a bad
+ * dim / L). */
+size_t ea_srv_tile_bytes(int dim, int L);
+
+/* The server's context (its chains by lane), for inspection; owned by the server. */
+int ea_srv_context(ea_srv *srv, ea_ctx **ctx);
 
 /* ------------------------------------------------------------------ no allocation
  * The paper has no counterpart to this entry point: it serves callers that cannot allocate

@@ -1,15 +1,24 @@
 """Self-written autotuner for the batched MUCA sweep launch (a8).
 
-The knobs are the ones muca_set_launch exposes: persistent work-queue grid vs one block per
-tile, the number of resident blocks per SM of the persistent grid (chains are latency-bound,
-so tiles sharing an SM sub-partition slow each other down), and sweeps per launch.  A
-candidate is timed with CUDA events on a scratch context with the same composition of tiles
-(same dim, L and chain counts, a different seed), so tuning never advances the caller's
-chains, whose results do not depend on the choice anyway.  The winner is cached in a JSON
-file keyed by the GPU name and the composition.
+Knobs:
+  * chains per tile for each lattice size (muca_set_tile_width): 32, or 16 where the narrow tile
+    brings the acceptance thresholds into shared memory (L = 7, 8).  A narrow tile runs each of
+    its chains faster but holds half as many, so it wins when the batch is smaller than what the
+    GPU can hold and loses when tiles queue for SMs;
+  * the persistent work-queue grid vs one block per tile, and the resident blocks per SM of the
+    persistent grid (chains are latency-bound, so tiles sharing an SM sub-partition slow each
+    other down);
+  * sweeps per launch.
+A candidate is timed with CUDA events on a scratch context with the same composition of chains
+(same dim, L and chain counts, a different seed), so tuning never advances the caller's chains,
+whose results do not depend on the choice anyway.  The winner is cached in a JSON file keyed by
+the GPU name and the composition.  Tile widths fix the layout, so they are chosen before the
+caller's chains are created: tune() first, then prepare(ctx, best) before ea_init_disorder and
+launch(ctx, best) after it (apply() does the last two for a context that has no chains yet).
 """
 from __future__ import annotations
 
+import itertools
 import json
 import os
 from pathlib import Path
@@ -18,7 +27,7 @@ from . import eamc
 from .build import BUILD
 
 CACHE = BUILD / "autotune.json"
-CANDIDATES = [
+LAUNCHES = [
     {"persistent": False, "blocks_per_sm": 0, "sweeps_per_launch": 0},
     {"persistent": True, "blocks_per_sm": 1, "sweeps_per_launch": 0},
     {"persistent": True, "blocks_per_sm": 2, "sweeps_per_launch": 0},
@@ -30,6 +39,16 @@ CANDIDATES = [
 def signature(groups) -> str:
     """groups: list of (dim, L, n_chains)."""
     return ";".join(f"{d}x{L}x{n}" for d, L, n in groups)
+
+
+def width_options(groups):
+    """Tile-width assignments to try: every L at 32, and each L that has a narrow width either
+    way (all combinations; at most a few sizes have one)."""
+    narrow = sorted({(d, L) for d, L, _ in groups if eamc.narrow_width(d, L) != 32})
+    out = []
+    for pick in itertools.product((False, True), repeat=len(narrow)):
+        out.append({str(L): (eamc.narrow_width(d, L) if p else 32) for (d, L), p in zip(narrow, pick)})
+    return out
 
 
 def _load():
@@ -47,42 +66,58 @@ def _store(db):
 
 
 def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, device: int = 0):
-    """Returns the fastest launch configuration for this composition of tiles."""
+    """Returns the fastest configuration for this composition of chains:
+    {"widths": {L: width}, "persistent", "blocks_per_sm", "sweeps_per_launch"}."""
     import torch
     key = f"{torch.cuda.get_device_name(device)}|{signature(groups)}|{sweeps}"
     db = _load() if use_cache else {}
     if key in db:
         return db[key]["best"]
     stream = torch.cuda.Stream(device=device)
-    ctx = eamc.Context(seed=0x5EED, device=device, stream=stream.cuda_stream)
-    rid = 0
-    for dim, L, n in groups:
-        ctx.init_disorder(dim, L, n, rid0=rid)
-        rid += n
     results = []
-    for cand in CANDIDATES:
-        ctx.set_launch(cand["persistent"], cand["sweeps_per_launch"], cand["blocks_per_sm"])
-        ctx.run_sweeps(max(2, sweeps // 8))  # warm-up
-        best = None
-        for _ in range(repeats):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.run_sweeps(sweeps)
-            e1.record(stream)
-            stream.synchronize()
-            ms = e0.elapsed_time(e1)
-            best = ms if best is None else min(best, ms)
-        results.append({**cand, "ms": best})
-    ctx.close()
+    for widths in width_options(groups):
+        ctx = eamc.Context(seed=0x5EED, device=device, stream=stream.cuda_stream)
+        for L, w in widths.items():
+            ctx.set_tile_width(int(L), w)
+        rid = 0
+        for dim, L, n in groups:
+            ctx.init_disorder(dim, L, n, rid0=rid)
+            rid += n
+        for cand in LAUNCHES:
+            ctx.set_launch(cand["persistent"], cand["sweeps_per_launch"], cand["blocks_per_sm"])
+            ctx.run_sweeps(max(2, sweeps // 8))  # warm-up
+            best = None
+            for _ in range(repeats):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.run_sweeps(sweeps)
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            results.append({"widths": widths, **cand, "ms": best})
+        ctx.close()
     winner = min(results, key=lambda r: r["ms"])
-    best = {k: winner[k] for k in ("persistent", "blocks_per_sm", "sweeps_per_launch")}
+    best = {k: winner[k] for k in ("widths", "persistent", "blocks_per_sm", "sweeps_per_launch")}
     if use_cache:
         db[key] = {"best": best, "trials": results}
         _store(db)
     return best
 
 
-def apply(ctx: "eamc.Context", groups, **kw):
-    best = tune(groups, **kw)
+def prepare(ctx: "eamc.Context", best):
+    """Tile widths of the chosen configuration (before the chains are created)."""
+    for L, w in best.get("widths", {}).items():
+        ctx.set_tile_width(int(L), int(w))
+
+
+def launch(ctx: "eamc.Context", best):
     ctx.set_launch(best["persistent"], best["sweeps_per_launch"], best["blocks_per_sm"])
+
+
+def apply(ctx: "eamc.Context", groups, **kw):
+    """Tunes for `groups` and configures ctx, which must not hold chains yet."""
+    best = tune(groups, **kw)
+    prepare(ctx, best)
+    launch(ctx, best)
     return best

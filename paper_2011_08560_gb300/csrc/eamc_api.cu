@@ -356,11 +356,12 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     ctx_drop_graph(ctx);  // the arenas may move and the tile set changes
     int smem_optin = 0;
     EA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    if (sweep_smem_bytes(dim, L) > (size_t)smem_optin)
+    const int W = sweep_width_supported(dim, L, ctx->tile_width[L]) ? ctx->tile_width[L] : kTile;
+    if (sweep_smem_bytes(dim, L, W) > (size_t)smem_optin)
         return fail(EA_EINVAL, "L=%d needs %zu bytes of shared memory per block, the device allows %d", L,
-                    sweep_smem_bytes(dim, L), smem_optin);
+                    sweep_smem_bytes(dim, L, W), smem_optin);
     const int V = volume_of(dim, L), B = rows_of(dim, L);
-    const int new_tiles = (n + kTile - 1) / kTile;
+    const int new_tiles = (n + W - 1) / W;
     const int tile0 = (int)ctx->tiles.size();
     const int chain_first = (int)ctx->chain_slot.size();
 
@@ -373,8 +374,10 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
         td.L = L;
         td.V = V;
         td.B = B;
-        td.n_active = std::min(kTile, n - t * kTile);
+        td.n_active = std::min(W, n - t * W);
         td.sweep_mul = 1;
+        td.width = W;
+        td.pad = 0;
         td.w_base = w_used;
         td.spin_off = spin_used;
         td.bond_off = bond_used;
@@ -400,7 +403,8 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     for (size_t s = 0; s < hs.size(); ++s) {
         SlotState &ss = hs[s];
         std::memset(&ss, 0, sizeof ss);
-        const int k = (int)s;  // index within this group
+        // chain index within this group (slots beyond the tile width stay inactive)
+        const int k = (int)(s / kTile) * W + std::min((int)(s % kTile), W - 1);
         ss.rid = rid0 + (uint32_t)std::min(k, n - 1);
         ss.stream = stream;
         ss.kind = EA_FLAT;
@@ -438,11 +442,11 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     ctx->bond_used = bond_used;
     ctx->w_used = w_used;
     ctx->max_V = std::max(ctx->max_V, V);
-    ctx->sweep_smem = std::max(ctx->sweep_smem, sweep_smem_bytes(dim, L));
+    ctx->sweep_smem = std::max(ctx->sweep_smem, sweep_smem_bytes(dim, L, W));
     for (int k = 0; k < n; ++k) {
-        const int slot = (tile0 + k / kTile) * kTile + k % kTile;
+        const int slot = (tile0 + k / W) * kTile + k % W;
         ctx->chain_slot.push_back(slot);
-        ctx->chain_woff.push_back(nt[k / kTile].w_base + (uint64_t)(k % kTile) * B);
+        ctx->chain_woff.push_back(nt[k / W].w_base + (uint64_t)(k % W) * B);
         ctx->chain_btop.push_back(0);
     }
     if ((rc = ctx_refresh_chains(ctx))) return rc;
@@ -672,6 +676,24 @@ extern "C" int muca_set_sweep_multiplier(ea_ctx *ctx, int L, int multiplier) {
         }
     if (!any) return fail(EA_EINVAL, "no tile of L=%d", L);
     EA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return EA_OK;
+}
+
+extern "C" int muca_set_tile_width(ea_ctx *ctx, int L, int width) {
+    if (!ctx) return fail(EA_EINVAL, "null context");
+    if (L < 3 || L > 12) return fail(EA_EINVAL, "L must be in [3, 12] (got %d)", L);
+    const int dim = ctx->dim ? ctx->dim : 3;
+    if (!sweep_width_supported(dim, L, width))
+        return fail(EA_EINVAL, "tile width %d is not available for dim=%d, L=%d (32 always; 16 for L=7,8 "
+                               "in 3D)", width, dim, L);
+    ctx->tile_width[L] = width;
+    return EA_OK;
+}
+
+extern "C" int muca_get_tile_width(int dim, int L, int width, size_t *smem_bytes, int *thresholds_in_smem) {
+    if (!sweep_width_supported(dim, L, width)) return fail(EA_EINVAL, "tile width %d unavailable", width);
+    if (smem_bytes) *smem_bytes = sweep_smem_bytes(dim, L, width);
+    if (thresholds_in_smem) *thresholds_in_smem = sweep_thresholds_in_smem(dim, L, width) ? 1 : 0;
     return EA_OK;
 }
 
@@ -978,7 +1000,7 @@ extern "C" int ea_synchronize(ea_ctx *ctx) {
 // ------------------------------------------------------------------------------ snapshots
 namespace {
 constexpr uint64_t kSnapMagic = 0x45414d43534e4150ull;  // "EAMCSNAP"
-constexpr uint32_t kSnapVersion = 2;
+constexpr uint32_t kSnapVersion = 3;
 
 struct SnapHeader {
     uint64_t magic;

@@ -46,6 +46,7 @@ struct ea_ctx {
     int persistent = 0;               // 1: resident grid pulling tiles from a queue
     uint64_t sweeps_per_launch = 0;   // 0: all requested sweeps in one launch
     int blocks_per_sm = 0;            // persistent grid: resident blocks per SM (0: occupancy limit)
+    int tile_width[13] = {32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32};  // chains per tile by L
     int n_sm = 0;
     int32_t *d_order = nullptr;       // tile ids, longest tiles first
     size_t order_cap = 0;

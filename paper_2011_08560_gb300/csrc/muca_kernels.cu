@@ -6,8 +6,8 @@
 //   quantize_kernel        a4: ln W -> u32 acceptance thresholds
 //   build_ensemble_kernel  a5: flat / power-law / 1/k / canonical weights from ln Omega
 //
-// One warp = one tile of 32 chains of equal (dim, L); in global memory the tile's lattice is
-// multi-spin coded (bit `lane` of each word is chain `lane`).
+// One warp = one tile of up to 32 chains of equal (dim, L); in global memory the tile's lattice
+// is multi-spin coded (bit `lane` of each word is chain `lane`).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,7 +44,7 @@ init_kernel(const TileDesc *__restrict__ tiles, int tile0, SlotState *__restrict
     const int L = td.L, V = td.V, nb = DIM * V;
     SlotState ss = slots[tile * kTile + lane];
     const bool active = lane < td.n_active;
-    const int row = in_row0 + blockIdx.x * kTile + lane;  // row in the caller's arrays
+    const int row = in_row0 + blockIdx.x * td.width + lane;  // row in the caller's arrays
     uint32_t *sp = spins + td.spin_off;
     uint32_t *bd = bonds + td.bond_off;
 
@@ -279,10 +279,10 @@ __device__ void update_weights_one(const TileDesc *__restrict__ tiles, SlotState
     }
 }
 
-__global__ void quantize_kernel(const TileDesc *__restrict__ tiles,
-                                const SlotState *__restrict__ slots,
-                                const double *__restrict__ lnW, uint32_t *__restrict__ thr) {
-    const int slot = blockIdx.x;
+__device__ __forceinline__ void quantize_one(const TileDesc *__restrict__ tiles,
+                                             const SlotState *__restrict__ slots,
+                                             const double *__restrict__ lnW, uint32_t *__restrict__ thr,
+                                             int slot) {
     const TileDesc td = tiles[slot / kTile];
     const int lane = slot % kTile;
     const SlotState ss = slots[slot];
@@ -309,6 +309,12 @@ __global__ void quantize_kernel(const TileDesc *__restrict__ tiles,
         dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
         dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
     }
+}
+
+__global__ void quantize_kernel(const TileDesc *__restrict__ tiles,
+                                const SlotState *__restrict__ slots,
+                                const double *__restrict__ lnW, uint32_t *__restrict__ thr) {
+    quantize_one(tiles, slots, lnW, thr, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------ a5
@@ -486,6 +492,158 @@ __global__ void reset_rt_kernel(const TileDesc *__restrict__ tiles, int n_slots,
     slots[slot] = ss;
 }
 
+// ------------------------------------------------------------------------------ a9 serving
+// Per-tick control of the served jobs, one thread per slot, after the tick's sweep launch.  A
+// job's schedule is counted in its own ticks (every tick adds its sweeps_per_tick sweeps to the
+// chain), so what a job computes does not depend on the jobs that share the device:
+//   iterate: every ticks_per_step ticks one weight step (Sec. II); after iter_steps steps the
+//            round-trip record restarts with E_g = the lowest energy seen and production begins;
+//   produce: a chain that went below E_g is requeued (Sec. III: new E_g, one more weight step,
+//            counting restarts) up to max_requeues times; the job is done at rt_target round
+//            trips, censored after max_prod_ticks production ticks;
+//   a descent that got stuck at admission leaves the chain inactive: the job fails.
+// A finished job writes one record into the completion ring and its chain stops.
+__global__ void srv_control_kernel(const TileDesc *__restrict__ tiles, int n_slots, SlotState *__restrict__ slots,
+                                   JobCtl *__restrict__ ctl, int32_t *__restrict__ flag,
+                                   SrvRecord *__restrict__ ring, uint32_t *__restrict__ head, uint32_t ring_cap,
+                                   unsigned long long *__restrict__ attempts, uint64_t tick) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n_slots) return;
+    flag[slot] = 0;
+    JobCtl c = ctl[slot];
+    if (c.phase != kJobIterate && c.phase != kJobProduce) return;
+    SlotState ss = slots[slot];
+    const TileDesc td = tiles[slot / kTile];
+    const int nb = td.dim * td.V;
+    int status = 0, f = 0;
+    if (!ss.active) {
+        status = kJobFailed;
+    } else {
+        c.ticks += 1;
+        atomicAdd(attempts, (unsigned long long)td.V * (unsigned long long)c.sweeps_per_tick);
+        if (c.phase == kJobIterate) {
+            if (c.ticks % c.ticks_per_step == 0) {
+                f = kFlagUpdate;
+                c.steps_done += 1;
+                if (c.steps_done >= c.iter_steps) {
+                    f |= kFlagResetRt;
+                    c.phase = kJobProduce;
+                    c.prod_ticks = 0;
+                }
+            }
+        } else {
+            c.prod_ticks += 1;
+            if (ss.requeue && c.requeues < c.max_requeues) {
+                f = kFlagUpdate | kFlagResetRt;
+                c.requeues += 1;
+                c.prod_ticks = 0;
+            } else if (ss.n_rt >= c.rt_target) {
+                status = kJobDone;
+            } else if (c.prod_ticks >= c.max_prod_ticks) {
+                status = kJobCensored;
+            }
+        }
+    }
+    if (status) {
+        SrvRecord r;
+        r.job = c.job;
+        r.status = status;
+        r.slot = slot;
+        r.n_rt = ss.n_rt;
+        r.requeues = c.requeues;
+        r.t_first = ss.t_first;
+        r.t_last = ss.t_last;
+        r.e_g = ss.e_g;
+        r.e_min = energy_of_bin(nb, ss.parity, ss.b_min);
+        r.sweeps = ss.t;
+        r.tick = tick;
+        const uint32_t k = atomicAdd(head, 1u);
+        ring[k % ring_cap] = r;
+        c.phase = kJobFinished;
+        ss.active = 0;
+        slots[slot] = ss;
+    }
+    flag[slot] = f;
+    ctl[slot] = c;
+}
+
+// weight step of the flagged slots (block per slot), then the round-trip record restarts where
+// asked: phase 0, no round trips, the lowest energy from now on; E_g stays as the step set it
+__global__ void srv_update_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                  double *__restrict__ lnW, uint32_t *__restrict__ hist,
+                                  double2 *__restrict__ acc, const int32_t *__restrict__ flag) {
+    const int slot = blockIdx.x;
+    const int f = flag[slot];
+    if (!(f & kFlagUpdate)) return;
+    update_weights_one(tiles, slots, lnW, hist, acc, slot);
+    if (!(f & kFlagResetRt)) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SlotState ss = slots[slot];
+        ss.phase = 0;
+        ss.n_rt = 0;
+        ss.t_first = -1;
+        ss.t_last = -1;
+        ss.requeue = 0;
+        ss.b_min = ss.b;
+        slots[slot] = ss;
+    }
+}
+
+__global__ void quantize_flagged_kernel(const TileDesc *__restrict__ tiles, const SlotState *__restrict__ slots,
+                                        const double *__restrict__ lnW, uint32_t *__restrict__ thr,
+                                        const int32_t *__restrict__ flag) {
+    if (flag[blockIdx.x] == 0) return;
+    quantize_one(tiles, slots, lnW, thr, blockIdx.x);
+}
+
+// an admitted job: ensemble and recursion of its (freshly reset) chain, empty Berg
+// accumulators, the job's schedule; its thresholds are quantised next
+__global__ void srv_start_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots,
+                                 JobCtl *__restrict__ ctl, int32_t *__restrict__ flag, double2 *__restrict__ acc,
+                                 const SrvStart *__restrict__ start) {
+    const SrvStart j = start[blockIdx.x];
+    const int slot = j.slot;
+    const TileDesc td = tiles[slot / kTile];
+    if (acc) {
+        double2 *a = acc + td.w_base + (uint64_t)(slot % kTile) * td.B;
+        for (int b = threadIdx.x; b < td.B; b += blockDim.x) a[b] = make_double2(0.0, 0.0);
+    }
+    if (threadIdx.x != 0) return;
+    SlotState ss = slots[slot];
+    ss.kind = j.kind;
+    ss.alpha = j.alpha;
+    ss.pole = j.pole;
+    ss.recursion = j.recursion;
+    slots[slot] = ss;
+    JobCtl c;
+    c.job = j.job;
+    c.phase = kJobIterate;
+    c.sweeps_per_tick = j.sweeps_per_tick;
+    c.ticks = 0;
+    c.steps_done = 0;
+    c.iter_steps = j.iter_steps;
+    c.ticks_per_step = j.ticks_per_step;
+    c.prod_ticks = 0;
+    c.max_prod_ticks = j.max_prod_ticks;
+    c.requeues = 0;
+    c.max_requeues = j.max_requeues;
+    c.rt_target = j.rt_target;
+    c.pad = 0;
+    ctl[slot] = c;
+    flag[slot] = kFlagQuantize;
+}
+
+__global__ void srv_cancel_kernel(SlotState *__restrict__ slots, JobCtl *__restrict__ ctl,
+                                  const int32_t *__restrict__ slot_of, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int slot = slot_of[k];
+    ctl[slot].phase = kJobIdle;
+    ctl[slot].job = 0;
+    slots[slot].active = 0;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ launchers
@@ -561,6 +719,46 @@ cudaError_t launch_reset_rt(const TileDesc *d_tiles, int n_tiles, SlotState *d_s
     if (n_tiles <= 0) return cudaSuccess;
     const int n_slots = n_tiles * kTile;
     reset_rt_kernel<<<(n_slots + 127) / 128, 128, 0, st>>>(d_tiles, n_slots, d_slots, d_sel);
+    return cudaGetLastError();
+}
+
+}  // namespace eamc
+
+namespace eamc {
+
+cudaError_t launch_srv_control(const TileDesc *d_tiles, int n_slots, SlotState *d_slots, JobCtl *d_ctl,
+                               int32_t *d_flag, SrvRecord *d_ring, uint32_t *d_head, uint32_t ring_cap,
+                               unsigned long long *d_attempts, uint64_t tick, cudaStream_t st) {
+    if (n_slots <= 0) return cudaSuccess;
+    srv_control_kernel<<<(n_slots + 127) / 128, 128, 0, st>>>(d_tiles, n_slots, d_slots, d_ctl, d_flag, d_ring,
+                                                              d_head, ring_cap, d_attempts, tick);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srv_update(const TileDesc *d_tiles, int n_slots, SlotState *d_slots, double *d_lnW,
+                              uint32_t *d_hist, double2 *d_acc, const int32_t *d_flag, cudaStream_t st) {
+    if (n_slots <= 0) return cudaSuccess;
+    srv_update_kernel<<<n_slots, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_hist, d_acc, d_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_flagged(const TileDesc *d_tiles, int n_slots, const SlotState *d_slots,
+                                    const double *d_lnW, uint32_t *d_thr, const int32_t *d_flag, cudaStream_t st) {
+    if (n_slots <= 0) return cudaSuccess;
+    quantize_flagged_kernel<<<n_slots, 128, 0, st>>>(d_tiles, d_slots, d_lnW, d_thr, d_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srv_start(const TileDesc *d_tiles, SlotState *d_slots, JobCtl *d_ctl, int32_t *d_flag,
+                             double2 *d_acc, const SrvStart *d_start, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    srv_start_kernel<<<n, 128, 0, st>>>(d_tiles, d_slots, d_ctl, d_flag, d_acc, d_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srv_cancel(SlotState *d_slots, JobCtl *d_ctl, const int32_t *d_slot_of, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    srv_cancel_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_slots, d_ctl, d_slot_of, n);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,13 @@
 //
 // Acceptance thresholds thr[b][n] live in shared memory (lane-interleaved, conflict free)
 // when the table fits, otherwise they are read through L1 from global memory.
+//
+// Tile width.  A tile holds W = 32 or 16 chains.  With W < 32 the warp's lanes l, l + W, ...
+// all run chain l (same inputs, same arithmetic, same values written to the same shared-memory
+// words) and only lanes below W write to global memory.  A narrow tile needs W/32 of the shared
+// memory of a full one, which brings the threshold tables of L = 7, 8 into shared memory: fewer
+// chains per SM, but each attempt of a chain is faster -- the better choice when the batch has
+// fewer chains than the GPU can hold.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -73,8 +80,9 @@ __device__ __forceinline__ T rot_prev(T r) {
     return ((r << 4) | (r >> (4 * L - 4))) & width_mask<T, L>();
 }
 
-template <int DIM, int L>
+template <int DIM, int L, int W>
 struct Geo {
+    static_assert(W == 32 || W == 16 || W == 8, "tile width");
     using T = RowT<L>;
     static constexpr int NR = DIM == 3 ? L * L : L;          // rows along x
     static constexpr int V = NR * L;
@@ -85,10 +93,10 @@ struct Geo {
     static constexpr int HQ = SUMQ + NG;                     // uint4 slots per lane per row
     static constexpr int LAG = (L >= 4 && L <= 8) ? 2 : 1;  // rows the producers run ahead
     static constexpr int NBUF = LAG + 1;                      // records in the ring
-    static constexpr size_t LATTICE_BYTES = (size_t)FIELDS * NR * 32 * sizeof(T);
-    static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * 32 * 16;
-    static constexpr size_t RES_BYTES = (size_t)2 * L * 32 * sizeof(int);  // row offsets for warp 4
-    static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * 32 * sizeof(uint32_t);
+    static constexpr size_t LATTICE_BYTES = (size_t)FIELDS * NR * W * sizeof(T);
+    static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * W * 16;
+    static constexpr size_t RES_BYTES = (size_t)2 * L * W * sizeof(int);  // row offsets, measurement
+    static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * W * sizeof(uint32_t);
     static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES;
     // up to 225 KB of the 227 KB a block may use (the rest: static shared memory)
     static constexpr bool SMEM_THR = BASE_BYTES + THR_BYTES <= 225 * 1024;
@@ -101,23 +109,24 @@ __device__ __forceinline__ uint32_t load_thr(const uint32_t *p) {
     else return __ldg(p);
 }
 
-template <class T>
-__device__ __forceinline__ void put4(uint4 *slots, int q, int lane, T a, T b, T c, T d) {
+// record slot q of chain ln in a ring buffer of W-chain-wide uint4 slots
+template <int W, class T>
+__device__ __forceinline__ void put4(uint4 *slots, int q, int ln, T a, T b, T c, T d) {
     if constexpr (sizeof(T) == 4) {
-        slots[q * 32 + lane] = make_uint4(a, b, c, d);
+        slots[q * W + ln] = make_uint4(a, b, c, d);
     } else {
-        slots[q * 32 + lane] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
-        slots[(q + 1) * 32 + lane] = make_uint4((uint32_t)c, (uint32_t)(c >> 32), (uint32_t)d, (uint32_t)(d >> 32));
+        slots[q * W + ln] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+        slots[(q + 1) * W + ln] = make_uint4((uint32_t)c, (uint32_t)(c >> 32), (uint32_t)d, (uint32_t)(d >> 32));
     }
 }
 
-template <class T>
-__device__ __forceinline__ void get4(const uint4 *slots, int q, int lane, T &a, T &b, T &c, T &d) {
+template <int W, class T>
+__device__ __forceinline__ void get4(const uint4 *slots, int q, int ln, T &a, T &b, T &c, T &d) {
     if constexpr (sizeof(T) == 4) {
-        const uint4 v = slots[q * 32 + lane];
+        const uint4 v = slots[q * W + ln];
         a = v.x; b = v.y; c = v.z; d = v.w;
     } else {
-        const uint4 v = slots[q * 32 + lane], w = slots[(q + 1) * 32 + lane];
+        const uint4 v = slots[q * W + ln], w = slots[(q + 1) * W + ln];
         a = ((T)v.y << 32) | v.x; b = ((T)v.w << 32) | v.z;
         c = ((T)w.y << 32) | w.x; d = ((T)w.w << 32) | w.z;
     }
@@ -136,7 +145,7 @@ __device__ __forceinline__ void get4(const uint4 *slots, int q, int lane, T &a, 
 // Running LAG rows ahead is exact as long as every row a record reads as final has been swept:
 // besides the -y row (which the consumer adds itself), the last row of a plane (y = L-1) reads
 // the plane's first row, L-1 rows back, so LAG <= L-2; the -z row is L rows back.
-template <int DIM, int L>
+template <int DIM, int L, int W>
 __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotState *__restrict__ slots,
                                            uint32_t *__restrict__ spins,
                                            const uint32_t *__restrict__ bonds,
@@ -144,22 +153,26 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
                                            uint32_t *__restrict__ hist, uint64_t n_sweeps,
                                            PhiloxKey key, int count_rt, unsigned *__restrict__ diag,
                                            unsigned char *smem_raw) {
-    using G = Geo<DIM, L>;
+    using G = Geo<DIM, L, W>;
     using T = typename G::T;
     constexpr int NR = G::NR, LAG = G::LAG, NBUF = G::NBUF;
     constexpr T NIB = nib_mask<T, L>();
     constexpr T LASTNIB = T(1) << (4 * (L - 1));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // ln: this lane's chain in the tile; lanes ln, ln + W, ... run the same chain and only the
+    // first (lane < W, `owner`) writes to global memory
+    const int ln = lane & (W - 1);
+    const bool owner = lane < W;
 
-    // ---- stage the lattice as nibble-packed row words, lane-interleaved: word k of lane l
-    //      at [k*32 + l].  Nibble x of a row word is site x of that row.
+    // ---- stage the lattice as nibble-packed row words, chain-interleaved: word k of chain ln
+    //      at [k*W + ln].  Nibble x of a row word is site x of that row.
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *Rs = sm;                  // spins, nibble = 1 if S = -1
-    T *JXs = sm + NR * 32;       // bond (x, x+1) has J = -1
-    T *JYs = sm + 2 * NR * 32;   // bond (x,y)-(x,y+1)
-    T *JZs = sm + 3 * NR * 32;   // bond (x,y,z)-(x,y,z+1)   (DIM == 3)
+    T *JXs = sm + NR * W;        // bond (x, x+1) has J = -1
+    T *JYs = sm + 2 * NR * W;    // bond (x,y)-(x,y+1)
+    T *JZs = sm + 3 * NR * W;    // bond (x,y,z)-(x,y,z+1)   (DIM == 3)
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
-    int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2][L][32]
+    int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2][L][W]
     const uint32_t *gsp = spins + td.spin_off;
     const uint32_t *gbd = bonds + td.bond_off;
     for (int row = warp; row < NR; row += kWarps) {
@@ -167,43 +180,46 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
 #pragma unroll
         for (int x = 0; x < L; ++x) {
             const int i = row * L + x;
-            r |= T((gsp[i] >> lane) & 1u) << (4 * x);
-            jx |= T((gbd[i * DIM + 0] >> lane) & 1u) << (4 * x);
-            jy |= T((gbd[i * DIM + 1] >> lane) & 1u) << (4 * x);
-            if constexpr (DIM == 3) jz |= T((gbd[i * DIM + 2] >> lane) & 1u) << (4 * x);
+            r |= T((gsp[i] >> ln) & 1u) << (4 * x);
+            jx |= T((gbd[i * DIM + 0] >> ln) & 1u) << (4 * x);
+            jy |= T((gbd[i * DIM + 1] >> ln) & 1u) << (4 * x);
+            if constexpr (DIM == 3) jz |= T((gbd[i * DIM + 2] >> ln) & 1u) << (4 * x);
         }
-        Rs[row * 32 + lane] = r;
-        JXs[row * 32 + lane] = jx;
-        JYs[row * 32 + lane] = jy;
-        if constexpr (DIM == 3) JZs[row * 32 + lane] = jz;
+        Rs[row * W + ln] = r;
+        JXs[row * W + ln] = jx;
+        JYs[row * W + ln] = jy;
+        if constexpr (DIM == 3) JZs[row * W + ln] = jz;
     }
 
-    const int slot = tile * kTile + lane;
+    const int slot = tile * kTile + ln;
     SlotState ss = slots[slot];
     const bool active = ss.active != 0;
-    const uint64_t lrow = td.w_base + (uint64_t)lane * G::B;
-    // element (b, n) of this lane's table at byte offset b * RSB + n * NSB from `tab`; rows
+    const uint64_t lrow = td.w_base + (uint64_t)ln * G::B;
+    // element (b, n) of this chain's table at byte offset b * RSB + n * NSB from `tab`; rows
     // -DIM .. B-1+DIM are addressable (padding), so a speculative row one move away from a
     // valid row never needs a clamp
-    constexpr int NSB = G::SMEM_THR ? 128 : 4;
+    constexpr int NSB = G::SMEM_THR ? 4 * W : 4;
     constexpr int RSB = 8 * NSB;
     const char *tab;
     if constexpr (G::SMEM_THR) {
         uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES + G::RES_BYTES);
         if (warp == 1) {
+            // the 32 / W lanes of a chain stage every (32 / W)-th bin each
+            constexpr int NM = 32 / W;
+            const int mi = lane / W;
             const uint4 *src = reinterpret_cast<const uint4 *>(thr + lrow * 8);
-            for (int b = 0; b < G::B; ++b) {
+            for (int b = mi; b < G::B; b += NM) {
                 const uint4 a = src[2 * b], c = src[2 * b + 1];
-                uint32_t *d = TH + (b + DIM) * 256 + lane;
-                d[0] = a.x; d[32] = a.y; d[64] = a.z; d[96] = a.w;
-                d[128] = c.x; d[160] = c.y; d[192] = c.z; d[224] = c.w;
+                uint32_t *d = TH + (b + DIM) * 8 * W + ln;
+                d[0] = a.x; d[W] = a.y; d[2 * W] = a.z; d[3 * W] = a.w;
+                d[4 * W] = c.x; d[5 * W] = c.y; d[6 * W] = c.z; d[7 * W] = c.w;
             }
-            for (int k = 0; k < DIM * 8; ++k) {
-                TH[k * 32 + lane] = 0u;
-                TH[((G::B + DIM) * 8 + k) * 32 + lane] = 0u;
+            for (int k = mi; k < DIM * 8; k += NM) {
+                TH[k * W + ln] = 0u;
+                TH[((G::B + DIM) * 8 + k) * W + ln] = 0u;
             }
         }
-        tab = reinterpret_cast<const char *>(TH + DIM * 256 + lane);
+        tab = reinterpret_cast<const char *>(TH + DIM * 8 * W + ln);
     } else {
         tab = reinterpret_cast<const char *>(thr + lrow * 8);
     }
@@ -215,7 +231,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     if (warp >= 1) {
         // ---- producers: record of row `row` (sweep index tt) into ring buffer `k`
         auto produce = [&](int row, int y, int z, uint32_t tt, int k) {
-            uint4 *buf = hand + k * G::HQ * 32;
+            uint4 *buf = hand + k * G::HQ * W;
             if (warp >= 2) {  // random words: Philox call g covers sites x = 4g .. 4g+3
                 // stored as min(r, 2^32 - 2) (an inactive chain: 2^32 - 1), so that the
                 // consumer's single test r < th is the rule "r < th or th = always" of an
@@ -229,33 +245,33 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
                     w.y = active ? min(w.y, kAlways - 1u) : kAlways;
                     w.z = active ? min(w.z, kAlways - 1u) : kAlways;
                     w.w = active ? min(w.w, kAlways - 1u) : kAlways;
-                    buf[(G::SUMQ + g) * 32 + lane] = w;
+                    buf[(G::SUMQ + g) * W + ln] = w;
                 }
                 return;
             }
             const int ryp = (y == L - 1) ? row - (L - 1) : row + 1;
-            const T R = Rs[row * 32 + lane];
-            const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * 32 + lane];  // bond (x, x+1) at nibble x
-            const T u_xm = rot_prev<T, L>(u_xp);                           // bond (x-1, x) at nibble x
-            T stable = (R ^ Rs[ryp * 32 + lane] ^ JYs[row * 32 + lane]) + (u_xp & ~LASTNIB);
+            const T R = Rs[row * W + ln];
+            const T u_xp = R ^ rot_next<T, L>(R) ^ JXs[row * W + ln];  // bond (x, x+1) at nibble x
+            const T u_xm = rot_prev<T, L>(u_xp);                        // bond (x-1, x) at nibble x
+            T stable = (R ^ Rs[ryp * W + ln] ^ JYs[row * W + ln]) + (u_xp & ~LASTNIB);
             if constexpr (DIM == 3) {
                 const int rzm = (z == 0) ? row + (L - 1) * L : row - L;
                 const int rzp = (z == L - 1) ? row - (L - 1) * L : row + L;
-                stable += (R ^ Rs[rzp * 32 + lane] ^ JZs[row * 32 + lane]) +
-                          (R ^ Rs[rzm * 32 + lane] ^ JZs[rzm * 32 + lane]);
+                stable += (R ^ Rs[rzp * W + ln] ^ JZs[row * W + ln]) +
+                          (R ^ Rs[rzm * W + ln] ^ JZs[rzm * W + ln]);
             }
             // the -y row: the consumer's previous row (added there) unless (3D, y = 0), where
             // it is the plane's last row, not yet swept
             T jym = 0;
             const int rym = (y == 0) ? row + (L - 1) : row - 1;
-            if (DIM == 3 && y == 0) stable += R ^ Rs[rym * 32 + lane] ^ JYs[rym * 32 + lane];
-            else jym = JYs[rym * 32 + lane];
+            if (DIM == 3 && y == 0) stable += R ^ Rs[rym * W + ln] ^ JYs[rym * W + ln];
+            else jym = JYs[rym * W + ln];
             const T sA = stable + u_xm;
             // nibble 0 of sB is never used (site 0 has no dynamic -x bond): its bit 3 carries
             // the stale wrap bond of site L-1
             const T wbit = (u_xp >> (4 * (L - 1))) & T(1);
             const T sB = ((stable + (u_xm ^ NIB)) & ~T(0xF)) | (wbit << 3);
-            put4<T>(buf, 0, lane, sA, sB, R, jym);
+            put4<W, T>(buf, 0, ln, sA, sB, R, jym);
         };
         int row = 0, y = 0, z = 0, kb = 0;
         uint64_t s = 0;
@@ -280,12 +296,12 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         uint64_t ms = 0;
         bool out_of_range = false;  // a bin outside [0, b_top]: a broken invariant, reported via diag
         auto measure = [&](int buf) {
-            const int *r = res + buf * L * 32 + lane;
+            const int *r = res + buf * L * W + ln;
             int lo = 0x7FFFFFFF, hi = -0x7FFFFFFF;
             uint32_t mtop = 0u, mbot = 0u;
 #pragma unroll
             for (int x = 0; x < L; ++x) {
-                const int pr = r[x * 32];
+                const int pr = r[x * W];
                 lo = min(lo, pr);
                 hi = max(hi, pr);
                 mtop |= (uint32_t)(pr >= topB) << x;
@@ -312,7 +328,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             if (++mrow == NR) {
                 mrow = 0;
                 ++ms;
-                if (active) atomicAdd(&hist_l[pnow / RSB], 1u);  // no return value: no wait
+                if (active && owner) atomicAdd(&hist_l[pnow / RSB], 1u);  // no return value: no wait
             }
         };
         for (uint64_t k = 0; k < total; ++k) {
@@ -336,7 +352,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             ss.t_last = tl;
             ss.t = t0 + n_sweeps;
             if (count_rt && active && energy_of_bin(DIM * G::V, ss.parity, ss.b_min) < ss.e_g) ss.requeue = 1;
-            slots[slot] = ss;
+            if (owner) slots[slot] = ss;
             if (diag && __any_sync(kFull, active && out_of_range) && lane == 0) atomicOr(diag, 1u);
         }
         return;
@@ -346,17 +362,17 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     // the previous attempt, applied lazily: row it was evaluated at (rq), row delta if it was
     // accepted (dq) and whether it was (pa)
     int rq = ss.b * RSB, dq = 0, pa = 0;
-    T Rprev = Rs[(NR - 1) * 32 + lane];
+    T Rprev = Rs[(NR - 1) * W + ln];
     int row = 0, y = 0, kb = 0;
     // the record of the row to sweep; with LAG >= 2 the next one is complete one barrier early
     // and is read while the current row runs
     T nsA, nsB, nR, njym;
     uint4 nrr[G::NG];
     auto load_rec = [&](int b) {
-        const uint4 *buf = hand + b * G::HQ * 32;
-        get4<T>(buf, 0, lane, nsA, nsB, nR, njym);
+        const uint4 *buf = hand + b * G::HQ * W;
+        get4<W, T>(buf, 0, ln, nsA, nsB, nR, njym);
 #pragma unroll
-        for (int g = 0; g < G::NG; ++g) nrr[g] = buf[(G::SUMQ + g) * 32 + lane];
+        for (int g = 0; g < G::NG; ++g) nrr[g] = buf[(G::SUMQ + g) * W + ln];
     };
     // candidate thresholds of the next attempt; with LAG >= 2 the last attempt of a row already
     // loads those of the next row's first attempt (its record is in registers by then)
@@ -379,7 +395,7 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
         }
         const int wbit = (int)((sB >> 3) & 1u);
         T accN = 0;  // nibble x = 1 if this chain flipped site x of the row
-        int *resb = res + (int)(k & 1) * L * 32 + lane;
+        int *resb = res + (int)(k & 1) * L * W + ln;
         // software pipeline: iteration x resolves attempt x from acc(x-1), issues both
         // candidate threshold loads of attempt x+1 (they need only acc(x-1)), then compares
         int nA = (int)(sA & 0xF), nB = nA;
@@ -434,13 +450,13 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             const uint32_t r = uint4_get(rr[x >> 2], x & 3);
             const bool acc = r < th;  // r clamped by the producer (see there)
             accN |= T(acc ? 1u : 0u) << (4 * x);
-            resb[x * 32] = acc ? rx + dx : rx;  // row offset after the attempt, for the measurement
+            resb[x * W] = acc ? rx + dx : rx;  // row offset after the attempt, for the measurement
             rq = rx;
             dq = dx;
             pa = acc ? 1 : 0;
         }
         const T Rfin = R ^ accN;
-        Rs[row * 32 + lane] = Rfin;
+        Rs[row * W + ln] = Rfin;
         Rprev = Rfin;
         if (++y == L) y = 0;
         if (++row == NR) {
@@ -450,17 +466,25 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
     }
     __syncthreads();
     // spins back to the multi-spin-coded global layout
+    constexpr uint32_t kOwned = W == 32 ? kFull : ((1u << W) - 1u);
     for (int r2 = 0; r2 < NR; ++r2) {
-        const T Rw = Rs[r2 * 32 + lane];
+        const T Rw = Rs[r2 * W + ln];
 #pragma unroll
         for (int x = 0; x < L; ++x) {
-            const uint32_t m = __ballot_sync(kFull, ((Rw >> (4 * x)) & 1u) != 0);
+            const uint32_t m = __ballot_sync(kFull, ((Rw >> (4 * x)) & 1u) != 0) & kOwned;
             if (lane == 0) spins[td.spin_off + r2 * L + x] = m;
         }
     }
 }
 
-// kWarps warps per tile of 32 chains; the tile's L selects the body.
+// Tile widths compiled per lattice size: 32 for every L; in 3D also 16 for L = 7, 8, whose
+// threshold tables then fit in shared memory.  (Width 8 would do the same for L = 9, 10, but
+// with both narrow families in this kernel it no longer fits in 255 registers without spills.)
+__host__ __device__ constexpr bool width_compiled(int dim, int L, int W) {
+    return W == 32 || (dim == 3 && W == 16 && (L == 7 || L == 8));
+}
+
+// kWarps warps per tile; the tile's (L, width) selects the body.
 // Direct mode (queue == nullptr): block b sweeps tile tile_list[b] (or b).  Persistent mode:
 // a grid sized to the resident capacity pulls positions of tile_list (longest tiles first)
 // from the counter *queue until n_work positions are taken.
@@ -471,10 +495,17 @@ __device__ __forceinline__ void sweep_one(const TileDesc *__restrict__ tiles, in
                                           unsigned *diag, unsigned char *smem_raw) {
     const TileDesc td = tiles[tile];
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
-#define EAMC_CASE(LL)                                                                      \
-    case LL:                                                                               \
-        sweep_tile<DIM, LL>(td, tile, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, \
-                            smem_raw);                                                           \
+#define EAMC_BODY(LL, WW) \
+    sweep_tile<DIM, LL, WW>(td, tile, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
+#define EAMC_CASE(LL)                                                              \
+    case LL:                                                                       \
+        if constexpr (width_compiled(DIM, LL, 16)) {                               \
+            if (td.width == 16) { EAMC_BODY(LL, 16); break; }                      \
+        }                                                                          \
+        if constexpr (width_compiled(DIM, LL, 8)) {                                \
+            if (td.width == 8) { EAMC_BODY(LL, 8); break; }                       \
+        }                                                                          \
+        EAMC_BODY(LL, 32);                                                         \
         break;
     switch (td.L) {
         EAMC_CASE(3) EAMC_CASE(4) EAMC_CASE(5) EAMC_CASE(6) EAMC_CASE(7)
@@ -482,6 +513,7 @@ __device__ __forceinline__ void sweep_one(const TileDesc *__restrict__ tiles, in
         default: break;
     }
 #undef EAMC_CASE
+#undef EAMC_BODY
 }
 
 template <int DIM>
@@ -510,26 +542,57 @@ muca_sweep_kernel(const TileDesc *__restrict__ tiles, const int32_t *__restrict_
     }
 }
 
-template <int DIM>
-size_t smem_for(int L) {
+template <int DIM, int W>
+size_t smem_for_w(int L) {
     switch (L) {
-        case 3: return Geo<DIM, 3>::SMEM;
-        case 4: return Geo<DIM, 4>::SMEM;
-        case 5: return Geo<DIM, 5>::SMEM;
-        case 6: return Geo<DIM, 6>::SMEM;
-        case 7: return Geo<DIM, 7>::SMEM;
-        case 8: return Geo<DIM, 8>::SMEM;
-        case 9: return Geo<DIM, 9>::SMEM;
-        case 10: return Geo<DIM, 10>::SMEM;
-        case 11: return Geo<DIM, 11>::SMEM;
-        case 12: return Geo<DIM, 12>::SMEM;
+        case 3: return Geo<DIM, 3, W>::SMEM;
+        case 4: return Geo<DIM, 4, W>::SMEM;
+        case 5: return Geo<DIM, 5, W>::SMEM;
+        case 6: return Geo<DIM, 6, W>::SMEM;
+        case 7: return Geo<DIM, 7, W>::SMEM;
+        case 8: return Geo<DIM, 8, W>::SMEM;
+        case 9: return Geo<DIM, 9, W>::SMEM;
+        case 10: return Geo<DIM, 10, W>::SMEM;
+        case 11: return Geo<DIM, 11, W>::SMEM;
+        case 12: return Geo<DIM, 12, W>::SMEM;
         default: return 0;
+    }
+}
+
+template <int DIM, int W>
+bool thr_smem_w(int L) {
+    switch (L) {
+        case 3: return Geo<DIM, 3, W>::SMEM_THR;
+        case 4: return Geo<DIM, 4, W>::SMEM_THR;
+        case 5: return Geo<DIM, 5, W>::SMEM_THR;
+        case 6: return Geo<DIM, 6, W>::SMEM_THR;
+        case 7: return Geo<DIM, 7, W>::SMEM_THR;
+        case 8: return Geo<DIM, 8, W>::SMEM_THR;
+        case 9: return Geo<DIM, 9, W>::SMEM_THR;
+        case 10: return Geo<DIM, 10, W>::SMEM_THR;
+        case 11: return Geo<DIM, 11, W>::SMEM_THR;
+        case 12: return Geo<DIM, 12, W>::SMEM_THR;
+        default: return false;
     }
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int dim, int L) { return dim == 3 ? smem_for<3>(L) : smem_for<2>(L); }
+size_t sweep_smem_bytes(int dim, int L, int width) {
+    if (!sweep_width_supported(dim, L, width)) return 0;
+    if (dim == 3) return width == 32 ? smem_for_w<3, 32>(L) : width == 16 ? smem_for_w<3, 16>(L) : smem_for_w<3, 8>(L);
+    return smem_for_w<2, 32>(L);
+}
+
+bool sweep_width_supported(int dim, int L, int width) {
+    return L >= 3 && L <= 12 && (dim == 2 || dim == 3) && width_compiled(dim, L, width);
+}
+
+bool sweep_thresholds_in_smem(int dim, int L, int width) {
+    if (!sweep_width_supported(dim, L, width)) return false;
+    if (dim == 3) return width == 32 ? thr_smem_w<3, 32>(L) : width == 16 ? thr_smem_w<3, 16>(L) : thr_smem_w<3, 8>(L);
+    return thr_smem_w<2, 32>(L);
+}
 
 // Raises the kernel's dynamic shared-memory limit when needed (a host call that is not stream
 // work, so it happens before any graph capture that launches the kernel).

@@ -86,6 +86,8 @@ __global__ void pack_kernel(int L, int n, const uint32_t *__restrict__ rid, cons
         td.B = B;
         td.n_active = min(kTile, n - tile * kTile);
         td.sweep_mul = 1;
+        td.width = kTile;
+        td.pad = 0;
         td.w_base = (uint64_t)tile * kTile * B;
         td.spin_off = spin_off;
         td.bond_off = bond_off;
@@ -176,7 +178,7 @@ extern "C" int muca_run_sweeps_noalloc(int dim, int L, int n, uint64_t seed, con
         return fail(EA_EINVAL, "null buffer");
     if (t0 > (1ull << 32) || n_sweeps > (1ull << 32) - t0)
         return fail(EA_EINVAL, "sweep counter would exceed 2^32");
-    const size_t smem = sweep_smem_bytes(dim, L);
+    const size_t smem = sweep_smem_bytes(dim, L, kTile);
     int dev = 0;
     NA_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(EA_EINVAL, "device %d out of range", dev);

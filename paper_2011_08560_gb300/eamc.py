@@ -50,6 +50,39 @@ class ea_pt_stats(ctypes.Structure):
                 ("e_min", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class ea_srv_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_L", ctypes.c_int32), ("Ls", ctypes.c_int32 * 16),
+                ("mem_budget", ctypes.c_size_t), ("base_sweeps", ctypes.c_int32),
+                ("poll_ticks", ctypes.c_int32), ("max_ahead", ctypes.c_int32)]
+
+
+class ea_job(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("rid", ctypes.c_uint32), ("stream", ctypes.c_uint32),
+                ("kind", ctypes.c_int32), ("recursion", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("pole", ctypes.c_double),
+                ("rt_target", ctypes.c_int32), ("iter_steps", ctypes.c_int32),
+                ("ticks_per_step", ctypes.c_int32), ("max_prod_ticks", ctypes.c_int32),
+                ("max_requeues", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class ea_srv_result(ctypes.Structure):
+    _fields_ = [("job_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("rid", ctypes.c_uint32), ("rt_target", ctypes.c_int32), ("n_rt", ctypes.c_int32),
+                ("requeues", ctypes.c_int32), ("t_first", ctypes.c_int64), ("t_last", ctypes.c_int64),
+                ("e_g", ctypes.c_int32), ("e_min", ctypes.c_int32), ("sweeps", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ea_srv_counters(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_uint64), ("ticks_read", ctypes.c_uint64), ("attempts", ctypes.c_uint64),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("done", ctypes.c_uint64), ("censored", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64), ("round_trips", ctypes.c_uint64),
+                ("mem_used", ctypes.c_size_t), ("seconds", ctypes.c_double)]
+
+
+EA_JOB_DONE, EA_JOB_CENSORED, EA_JOB_FAILED = 1, 2, 3
+
 P = ctypes.c_void_p
 _i, _u32, _u64, _f64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
 
@@ -83,12 +116,23 @@ SIGNATURES = {
     "muca_set_launch": (_i, [P, _i, _u64, _i]),
     "ea_reset_chains": (_i, [P, P, _i, P, P]),
     "muca_set_sweep_multiplier": (_i, [P, _i, _i]),
+    "muca_set_tile_width": (_i, [P, _i, _i]),
+    "muca_get_tile_width": (_i, [_i, _i, _i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i)]),
     "muca_update_weights_subset": (_i, [P, P, _i]),
     "muca_copy_weights": (_i, [P, P, P, _i]),
     "ea_graph_capture": (_i, [P, _i, _u64, _i, _i]),
     "ea_graph_launch": (_i, [P, _i]),
     "ea_graph_release": (_i, [P]),
     "muca_run_sweeps_noalloc": (_i, [_i, _i, _i, _u64, P, P, P, P, P, P, P, _u64, _u64, P]),
+    "ea_srv_create": (_i, [ctypes.POINTER(P), _i, P, _u64, ctypes.POINTER(ea_srv_config)]),
+    "ea_srv_destroy": (None, [P]),
+    "ea_srv_submit": (_i, [P, ctypes.POINTER(ea_job), ctypes.POINTER(_u64)]),
+    "ea_srv_cancel": (_i, [P, _u64]),
+    "ea_srv_step": (_i, [P, _i]),
+    "ea_srv_poll": (_i, [P, P, _i, ctypes.POINTER(_i), _i]),
+    "ea_srv_stats": (_i, [P, ctypes.POINTER(ea_srv_counters)]),
+    "ea_srv_context": (_i, [P, ctypes.POINTER(P)]),
+    "ea_srv_tile_bytes": (ctypes.c_size_t, [_i, _i]),
     "pt_init": (_i, [P, _i, _i, _i, _u32, _i, P, P]),
     "pt_set_rt_bounds": (_i, [P, P, P]),
     "pt_run": (_i, [P, _u64, _i]),
@@ -116,6 +160,23 @@ def lib() -> ctypes.CDLL:
             fn.restype = res
             fn.argtypes = args
     return _lib
+
+
+def tile_width_info(dim: int, L: int, width: int):
+    """(dynamic shared memory per sweep block, thresholds in shared memory?) for tiles of this
+    (dim, L, width), or None when that width is not available."""
+    smem, in_smem = ctypes.c_size_t(0), ctypes.c_int(0)
+    if lib().muca_get_tile_width(dim, L, width, ctypes.byref(smem), ctypes.byref(in_smem)) != EA_OK:
+        return None
+    return smem.value, bool(in_smem.value)
+
+
+def narrow_width(dim: int, L: int) -> int:
+    """The narrowest tile width available at (dim, L) (32 when there is no narrow one)."""
+    for w in (16,):
+        if tile_width_info(dim, L, w):
+            return w
+    return 32
 
 
 def check(rc: int) -> int:
@@ -301,6 +362,11 @@ class Context:
         r = np.ascontiguousarray(rids, dtype=np.uint32)
         s = np.ascontiguousarray(streams, dtype=np.uint32)
         check(lib().ea_reset_chains(self._h, _p(c), c.shape[0], _p(r), _p(s)))
+
+    def set_tile_width(self, L: int, width: int):
+        """Chains per tile (32, or 16 for L = 7, 8 in 3D) for chains of size L added
+        afterwards."""
+        check(lib().muca_set_tile_width(self._h, L, width))
 
     def set_sweep_multiplier(self, L: int, multiplier: int):
         check(lib().muca_set_sweep_multiplier(self._h, L, multiplier))

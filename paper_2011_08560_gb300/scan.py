@@ -57,6 +57,70 @@ class ScanResult:
         rows = [r for r in self.summary() if r["ensemble"].startswith("pl")]
         return min(rows, key=lambda r: r.get("tau_over_flat", math.inf))
 
+    def table_one(self, pt_tau=None, pt_below_eg=None, pl_label: str = "pl(-3.6,96)", eps: float = 1e-4,
+                  n_blocks: int = 16) -> dict:
+        """Table I of the paper on these realizations: for flat MUCA, the 1/k ensemble and (when
+        given) PT, r_pop and r_eps = ratio of the method's population / quantile mean round-trip
+        time to the power-law ensemble's, with jackknife errors.  Realizations where any method
+        found an energy below E_g are left out (the paper requeues them until none does), as are
+        realizations without a round trip in the method or in the power-law ensemble."""
+        k_pl = self.labels.index(pl_label)
+        bad = self.requeue.any(axis=0)
+        if pt_below_eg is not None:
+            bad = bad | np.asarray(pt_below_eg, dtype=bool)
+        out = {"excluded_below_eg": int(bad.sum()), "reference": pl_label, "eps": eps}
+        methods = [(lab, self.tau[self.labels.index(lab)]) for lab in ("flat", "1/k") if lab in self.labels]
+        if pt_tau is not None:
+            methods.append(("PT", np.asarray(pt_tau, dtype=float)))
+        for lab, tau in methods:
+            a, b = tau[~bad], self.tau[k_pl][~bad]
+            ok = np.isfinite(a) & np.isfinite(b)
+            if ok.sum() < 8:
+                out[lab] = {"pairs": int(ok.sum())}
+                continue
+            out[lab] = analysis.relative_performance(a, b, eps=eps, n_blocks=n_blocks)
+        return out
+
+
+def pt_round_trips(dim: int, L: int, n_real: int, M: int, e_g, seed: int = 0, rid0: int = 0,
+                   beta_min: float = 0.3, beta_max: float = 2.15, windows: int = 8, window: int = 1000,
+                   prod_sweeps: int = 20000, stream=None):
+    """PT on the same realizations (Sec. II, PT: M replicas, constant exchange rates imposed on each
+    realization during equilibration by moving its temperatures; T_max = 1 / beta_min > 3).  The
+    round trip runs between E_g (bottom, given per realization: the MUCA stage's lowest energy)
+    and E_hot, the mean energy at the hottest temperature over the equilibration (an energy
+    typical of a temperature well above freezing, Sec. III), per replica.  A realization's time
+    pools its replicas: tau_i = sum over replicas of (t_last - t_first) / sum of round trips.
+    Returns (tau [n_real] (inf: no round trip), below_eg [n_real]: a replica went below E_g)."""
+    from .workloads import geometric_betas
+    ctx = eamc.Context(seed=seed, stream=stream)
+    try:
+        ctx.pt_init(dim, L, n_real, geometric_betas(M, beta_min, beta_max), rid0=rid0)
+        hot = []
+        for w in range(windows):
+            for _ in range(10):
+                ctx.pt_run(window // 10)
+                _, E, _, _ = ctx.pt_state(spins=False)
+                hot.append(E[:, 0].astype(np.int64))
+            ctx.pt_adapt(0.5)
+        e_hot = np.floor(np.mean(hot, axis=0)).astype(np.int32)
+        e_g = np.ascontiguousarray(e_g, dtype=np.int32)
+        ctx.pt_roundtrips(reset=True)
+        ctx.pt_set_rt_bounds(e_g, e_hot)
+        ctx.pt_run(prod_sweeps, count_roundtrips=True)
+        recs = ctx.pt_roundtrips()
+    finally:
+        ctx.close()
+    tau = np.full(n_real, math.inf)
+    below = np.zeros(n_real, dtype=bool)
+    for r, reps in enumerate(recs):
+        n = sum(x["n_rt"] for x in reps)
+        span = sum(x["t_last"] - x["t_first"] for x in reps if x["n_rt"] > 0)
+        if n > 0:
+            tau[r] = span / n
+        below[r] = min(x["e_min"] for x in reps) < e_g[r]
+    return tau, below
+
 
 def profile_scan(dim: int, L: int, n_real: int, alphas, poles, seed: int = 0, rid0: int = 0,
                  dos_iters: int = 30, dos_sweeps: int = 2000, recursion: int = eamc.EA_REC_BERG,

@@ -19,15 +19,31 @@ class MucaWorkload:
     ensembles: tuple = ("flat",)
     alpha: float = -3.6          # paper's best power-law exponent (Sec. II)
     pole: float = 96.0           # paper's best pole offset Delta E (Sec. II)
-    sweeps: int = 10_000
+    sweeps: int = 10_000         # sweeps per timed step
+    # weight iteration before production: iter_steps updates after iter_sweeps sweeps each,
+    # with Berg's accumulated recursion ("berg") or the plain step ("plain")
+    iter_steps: int = 0
+    iter_sweeps: int = 0
+    recursion: str = "berg"
+    prod_sweeps: int = 0
 
 
-# L=4, one realization, flat MUCA: the small case the oracle finishes in seconds
-SMALL = MucaWorkload("3D +-J EA L=4, 1 realization, flat MUCA", 3, 4, 1, seed=1)
+# L=4, one realization, flat MUCA: 20 x 10^4 iteration sweeps, then 10^5 production sweeps;
+# the small case the oracle finishes in seconds
+SMALL = MucaWorkload("3D +-J EA L=4, 1 realization (seed 1), flat MUCA, 20 x 10^4 iteration + "
+                     "10^5 production sweeps", 3, 4, 1, seed=1, iter_steps=20, iter_sweeps=10_000,
+                     recursion="plain", prod_sweeps=100_000)
 
-# L=6, 1024 realizations, flat MUCA beside the power-law ensemble (the headline workload)
-HEADLINE = MucaWorkload("3D +-J EA L=6, 1024 realizations, flat MUCA + power-law MUCA", 3, 6,
-                        1024, seed=2, ensembles=("flat", "powerlaw"))
+# the headline: L=8, 1024 realizations, power-law MUCA (alpha = -3.6, Delta E = 96); weights
+# from Berg's recursion, then E_g fixed and round trips counted in production sweeps
+HEADLINE = MucaWorkload("3D +-J EA L=8, 1024 realizations, power-law MUCA (alpha=-3.6, "
+                        "Delta E=96), production with frozen weights", 3, 8, 1024, seed=2,
+                        ensembles=("powerlaw",), sweeps=10_000, iter_steps=60,
+                        iter_sweeps=10_000, recursion="berg")
+
+# L=6, 1024 realizations, flat MUCA beside the power-law ensemble (2048 chains)
+L6_FLAT_PL = MucaWorkload("3D +-J EA L=6, 1024 realizations, flat MUCA + power-law MUCA", 3, 6,
+                          1024, seed=2, ensembles=("flat", "powerlaw"))
 
 # PT baseline: L=8, 1024 realizations x 32 temperatures, geometric beta in [0.2, 3.0]
 PT = dict(dim=3, L=8, n_real=1024, M=32, beta_min=0.2, beta_max=3.0, seed=3)

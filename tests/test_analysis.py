@@ -60,3 +60,33 @@ def test_running_mean_and_jackknife():
     a, b = rng.exponential(3.0, 500), rng.exponential(1.5, 500)
     r, err = an.jackknife(a, b, np.mean)
     assert abs(r - 2.0) < 4 * err + 0.2 and err > 0
+
+
+def test_block_jackknife_reduces_to_leave_one_out():
+    rng = np.random.default_rng(4)
+    a, b = rng.exponential(3.0, 40), rng.exponential(1.5, 40)
+    assert an.block_jackknife(a, b, np.mean, n_blocks=40) == pytest.approx(an.jackknife(a, b, np.mean), rel=1e-12)
+    # the delete-one-block error of a mean ratio is close to the delta-method standard error
+    a, b = rng.exponential(3.0, 4000), rng.exponential(1.5, 4000)
+    r, err = an.block_jackknife(a, b, np.mean, n_blocks=20)
+    delta = r * math.sqrt(np.var(a) / a.size / np.mean(a) ** 2 + np.var(b) / b.size / np.mean(b) ** 2)
+    assert 0.5 * delta < err < 2.0 * delta
+
+
+def test_relative_performance_recovers_known_ratios():
+    """Paired samples from two Frechet laws: r_pop near the ratio of the distribution means,
+    r_eps near the ratio of the quantile means of the true parameters (Table I quantities);
+    realizations without a finite time in either method are left out."""
+    rng = np.random.default_rng(11)
+    pa, pb = (600.0, 250.0, 0.3), (200.0, 80.0, 0.25)
+    a = stats.genextreme(c=-pa[2], loc=pa[0], scale=pa[1]).rvs(size=3000, random_state=rng)
+    b = stats.genextreme(c=-pb[2], loc=pb[0], scale=pb[1]).rvs(size=3000, random_state=rng)
+    a[:7] = np.inf
+    out = an.relative_performance(a, b, eps=1e-4)
+    assert out["pairs"] == 2993
+    r_pop, e_pop = out["r_pop"]
+    r_eps, e_eps = out["r_eps"]
+    want_pop = an.distribution_mean(*pa) / an.distribution_mean(*pb)
+    want_eps = an.quantile_mean(*pa, 1e-4) / an.quantile_mean(*pb, 1e-4)
+    assert abs(r_pop - want_pop) < 4 * e_pop + 0.02 and e_pop > 0
+    assert abs(r_eps - want_eps) < 4 * e_eps + 0.02 and e_eps > 0

@@ -1,6 +1,8 @@
 """Parity at the benchmark's full sizes and launch configurations, on sampled chains.
 
-The headline batch (L=6, 1024 realizations x {flat, power law} = 2048 chains) and the uneven
+The headline batch (L=8, 1024 power-law chains: Berg weight iteration, E_g fixed, then a
+production step with round-trip counting), the L=6 batch (1024 realizations x {flat, power
+law} = 2048 chains) and the uneven
 batch (4096 realizations of L in {4..12} x {power law, flat, 1/k} = 12288 chains, autotuned
 launch, graph-captured iteration loop) are built by the same functions bench.py times; the
 oracle then replays chosen chains one by one through the same steps.  Spins, energies, round-
@@ -40,14 +42,55 @@ def _check(ctx, orc, c, ch, lnW):
 
 
 def test_headline_full_size_sampled(eamc, orc):
-    """Two bench steps (10^4 sweeps with round-trip counting, then a weight update) of the
-    headline batch; chains of both ensembles at both ends of the realization range."""
+    """The headline as bench.py builds and launches it: 1024 power-law chains of L=8 with Berg's
+    recursion, a (shortened) iteration phase, E_g fixed and records reset, then one production
+    step of 10^4 sweeps with round-trip counting; sampled chains replayed by the oracle."""
+    import dataclasses
+
     import torch
 
     import bench
-    from paper_2011_08560_gb300.workloads import HEADLINE as W
+    from paper_2011_08560_gb300.workloads import HEADLINE
+    W = dataclasses.replace(HEADLINE, iter_steps=4, iter_sweeps=1000)
     stream = torch.cuda.Stream()
-    ctx = bench.build_context(eamc, 0, stream.cuda_stream)
+    ctx = bench.build_context(eamc, 0, stream.cuda_stream, W)
+    assert ctx.num_chains() == W.n_real == 1024
+    bench.iterate_weights(ctx, W, stream)
+    with torch.cuda.stream(stream):
+        ctx.run_sweeps(W.sweeps, count_roundtrips=True)
+    ctx.synchronize()
+    H = ctx.histograms()
+    for rid in (0, 511, 1023):
+        ch = orc.Chain(W.dim, W.L, W.seed, rid, 0)
+        lnW = np.zeros(ch.b_top + 1)
+        acc = orc.berg_state(ch.b_top + 1)
+        for _ in range(W.iter_steps):
+            ch.sweeps(W.iter_sweeps, orc.quantize(W.dim, lnW))
+            lnW = orc.update_weights_berg(W.dim, W.L, ch.parity, orc.POWERLAW, W.alpha, W.pole,
+                                          ch.rt.e_min, lnW, ch.hist, acc)
+            ch.hist[:] = 0
+        # E_g fixed at the lowest energy; the record restarts at the current energy
+        ch.rt = orc.RT(phase=0, n_rt=0, t_first=-1, t_last=-1, e_min=ch.E, e_g=ch.rt.e_min,
+                       requeue=0, pad=0)
+        ch.sweeps(W.sweeps, orc.quantize(W.dim, lnW), count_rt=True)
+        _check(ctx, orc, rid, ch, lnW)
+        assert np.array_equal(H[rid, :ch.b_top + 1], ch.hist)
+    ctx.check()                       # no chain left its energy range on the device
+    ctx.close()
+
+
+def test_l6_full_size_sampled(eamc, orc):
+    """Two steps (10^4 sweeps with round-trip counting, then a weight update) of the L=6 batch
+    of 2048 chains; chains of both ensembles at both ends of the realization range."""
+    import torch
+
+    from paper_2011_08560_gb300.workloads import L6_FLAT_PL as W
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=W.seed, device=0, stream=stream.cuda_stream)
+    ctx.init_disorder(W.dim, W.L, W.n_real, rid0=0, stream=0)
+    ctx.init_disorder(W.dim, W.L, W.n_real, rid0=0, stream=1)
+    ctx.set_ensemble(0, W.n_real, eamc.EA_FLAT)
+    ctx.set_ensemble(W.n_real, W.n_real, eamc.EA_POWERLAW, W.alpha, W.pole)
     S = W.sweeps
     with torch.cuda.stream(stream):
         for _ in range(2):
@@ -65,7 +108,7 @@ def test_headline_full_size_sampled(eamc, orc):
             ch.hist[:] = 0
             ch.rt.e_g = ch.rt.e_min          # the update takes E_g = the lowest energy seen
         _check(ctx, orc, stream_id * n + rid, ch, lnW)
-    ctx.check()                       # no chain left its energy range on the device
+    ctx.check()
     ctx.close()
 
 

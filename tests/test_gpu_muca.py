@@ -100,6 +100,95 @@ def test_sweeps_bit_exact_with_injected_thresholds(eamc, orc, dim, L, n, sweeps)
         _compare_state(ctx, chains)
 
 
+def _injected_run(eamc, orc, ctx, chains, chain0, thr, sweeps, parts=2):
+    """Inject thresholds, set E_g a little below the start and sweep both sides in parts."""
+    n = len(chains)
+    ctx.set_thresholds(chain0, _pad(thr, max(len(t) for t in thr)))
+    eg = np.array([c.E - 8 for c in chains], dtype=np.int32)
+    ctx.set_eg(chain0, n, eg)
+    for c, e in zip(chains, eg):
+        c.rt.e_g = int(e)
+    done = 0
+    for k in range(parts):
+        part = sweeps // parts if k < parts - 1 else sweeps - done
+        ctx.run_sweeps(part, count_roundtrips=True)
+        for c, th in zip(chains, thr):
+            c.sweeps(part, th, count_rt=True)
+        done += part
+        _compare_state(ctx, chains, chain0)
+
+
+@pytest.mark.parametrize("L,n,sweeps", [(8, 32, 200), (9, 32, 200), (10, 32, 200), (11, 32, 200),
+                                        (12, 32, 200)])
+def test_large_lattices_full_tile(eamc, orc, L, n, sweeps):
+    """Full tiles at the sizes with thresholds read through L1 (L >= 7) and 64-bit row words
+    (L >= 9), with round-trip counting."""
+    rng = np.random.default_rng(1000 + L)
+    ctx = eamc.Context(seed=SEED)
+    ctx.init_disorder(3, L, n, rid0=200, stream=1)
+    chains = _oracle_chains(orc, 3, L, n, rid0=200, stream=1)
+    thr = [orc.quantize(3, _random_lnw(rng, c.b_top, 0.4)) for c in chains]
+    _injected_run(eamc, orc, ctx, chains, 0, thr, sweeps)
+    assert sum(c.rt.n_rt for c in chains) > 0 or L >= 11   # round trips exercised
+
+
+@pytest.mark.parametrize("L,n,sweeps", [(7, 19, 150), (8, 33, 200), (8, 16, 60)])
+def test_narrow_tiles_bit_exact(eamc, orc, L, n, sweeps):
+    """Tiles of 16 chains (thresholds in shared memory at L = 7, 8): ragged last tiles, the
+    same trajectories as the oracle."""
+    info = eamc.tile_width_info(3, L, 16)
+    assert info is not None and info[1], "width 16 keeps the thresholds in shared memory"
+    assert eamc.tile_width_info(3, L, 32)[1] is False
+    rng = np.random.default_rng(2000 + L + n)
+    ctx = eamc.Context(seed=SEED)
+    ctx.set_tile_width(L, 16)
+    ctx.init_disorder(3, L, n, rid0=300, stream=4)
+    chains = _oracle_chains(orc, 3, L, n, rid0=300, stream=4)
+    desc = ctx.describe()
+    for k, c in enumerate(chains):
+        assert desc[k]["rid"] == 300 + k and desc[k]["b_top"] == c.b_top
+    thr = [orc.quantize(3, _random_lnw(rng, c.b_top, 0.4)) for c in chains]
+    _injected_run(eamc, orc, ctx, chains, 0, thr, sweeps, parts=3)
+    ctx.check()
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_mixed_widths_in_one_context(eamc, orc, persistent):
+    """Narrow L = 8 tiles beside full L = 6 tiles and caller couplings, one launch; then the
+    plain weight iteration (thresholds requantised on the device)."""
+    ctx = eamc.Context(seed=SEED)
+    ctx.set_tile_width(8, 16)
+    J8 = np.stack([orc.make_disorder(3, 8, 5, 40 + k) for k in range(21)])
+    ctx.init_disorder(3, 8, 21, rid0=40, couplings=J8)
+    ctx.init_disorder(3, 6, 35, rid0=70, stream=2)
+    ctx.set_ensemble(0, 21, eamc.EA_POWERLAW, -3.6, 96.0)
+    ctx.set_launch(persistent, 0, 0)
+    chains = _oracle_chains(orc, 3, 8, 21, rid0=40, J=J8) + _oracle_chains(orc, 3, 6, 35, rid0=70, stream=2)
+    kinds = [orc.POWERLAW] * 21 + [orc.FLAT] * 35
+    lnW = [np.zeros(c.b_top + 1) for c in chains]
+    for _ in range(3):
+        ctx.run_sweeps(40)
+        ctx.update_weights()
+        for k, c in enumerate(chains):
+            c.sweeps(40, orc.quantize(3, lnW[k]))
+            lnW[k] = orc.update_weights(3, c.L, c.parity, kinds[k], -3.6, 96.0, c.rt.e_min, lnW[k], c.hist)
+            c.hist[:] = 0
+        _compare_state(ctx, chains, hist=True, rt=False)
+        G = ctx.get_weights()
+        for k, c in enumerate(chains):
+            assert _close(G[k, :c.b_top + 1], lnW[k])
+    ctx.check()
+
+
+def test_tile_width_rejects_unavailable(eamc):
+    ctx = eamc.Context(seed=SEED)
+    for L, w in ((6, 16), (12, 16), (8, 8), (8, 64)):
+        with pytest.raises(eamc.EamcError):
+            ctx.set_tile_width(L, w)
+    assert eamc.tile_width_info(3, 6, 16) is None
+    assert eamc.narrow_width(3, 8) == 16 and eamc.narrow_width(3, 6) == 32
+
+
 def test_zero_sweeps_and_errors(eamc, orc):
     ctx = eamc.Context(seed=SEED)
     with pytest.raises(eamc.EamcError):

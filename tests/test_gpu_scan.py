@@ -73,3 +73,35 @@ def test_profile_scan_matches_oracle(eamc, orc):
                 assert res.tau[k, r] == (ch.rt.t_last - ch.rt.t_first) / ch.rt.n_rt
     rows = res.summary()
     assert rows[0]["ensemble"] == "flat" and "tau_over_flat" not in rows[0]
+
+
+def test_pt_arm_matches_oracle(eamc, orc):
+    """The scan's PT arm (adapted temperatures, E_hot from the hottest slot, round trips between
+    E_g and E_hot per replica, replicas pooled per realization) against the oracle run through
+    the same steps, on sampled realizations of one 32-realization group."""
+    from paper_2011_08560_gb300 import scan
+    from paper_2011_08560_gb300.workloads import geometric_betas
+    dim, L, n, M, seed = 3, 4, 32, 4, 17
+    windows, window, prod = 2, 100, 600
+    e_g = np.array([-76 + 4 * (r % 3) for r in range(n)], dtype=np.int32)
+    tau, below = scan.pt_round_trips(dim, L, n, M, e_g, seed=seed, windows=windows, window=window,
+                                     prod_sweeps=prod)
+    for r in (0, 13, 31):
+        p = orc.PTRealization(dim, L, seed, r, geometric_betas(M, 0.3, 2.15))
+        hot = []
+        for _ in range(windows):
+            for _ in range(10):
+                p.sweeps(window // 10)
+                hot.append(int(p.E[0]))
+            p.adapt(0.5)
+        e_hot = int(np.floor(np.mean(hot)))
+        for k in range(M):
+            p.rt[p.label[k]] = orc.RT(phase=0, n_rt=0, t_first=-1, t_last=-1, e_min=int(p.E[k]),
+                                      e_g=0, requeue=0, pad=0)
+        p.sweeps(prod, count_rt=True, e_g=int(e_g[r]), e_hot=e_hot)
+        n_rt = sum(p.rt[m].n_rt for m in range(M))
+        span = sum(p.rt[m].t_last - p.rt[m].t_first for m in range(M) if p.rt[m].n_rt > 0)
+        want = span / n_rt if n_rt else np.inf
+        assert tau[r] == want, (r, tau[r], want)
+        assert bool(below[r]) == (min(p.rt[m].e_min for m in range(M)) < e_g[r])
+    assert np.isfinite(tau).sum() > 0
