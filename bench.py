@@ -50,9 +50,11 @@ LATENCY_FLOOR_CYCLES = 20.0
 # unsatisfied counts + 4 for the classes, about 8 compared bit planes (2 Philox4x32-10 calls of
 # 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
 PT_ALG_OPS = 4.7
-# dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch of the headline workload
-# from an ncu capture of this kernel version; None until one has been taken
-SWEEP_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one production launch of the headline workload
+# (L=8, 1024 chains in tiles of 16), ncu capture of this kernel version: 13.67 MB + 0 B for a
+# 2000-sweep launch.  It is the one-time staging of the threshold tables and lattices, so it
+# does not grow with the sweeps of a launch: a 10^4-sweep launch moves the same bytes.
+SWEEP_TRAFFIC_BYTES = 13.67e6
 
 
 def parse():
@@ -65,10 +67,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
-    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "recursion", "scan",
-                                       "small", "flat", "l6"],
+    ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
+                                       "recursion", "scan", "small", "flat", "l6", "table_one_l8"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner: narrow tiles where available, one launch per call "
+                         "(a fixed launch sequence, for profiling)")
     ap.add_argument("--iter-steps", type=int, default=None,
                     help="weight-iteration steps before timing (default: the workload's)")
     ap.add_argument("--iter-sweeps", type=int, default=None,
@@ -210,12 +215,16 @@ def headline(args):
 
 def build_context(eamc, rank: int, stream_ptr: int, W=HEADLINE, ensembles=None, tuned=True):
     """The chains of workload W (one per realization and ensemble, stream = ensemble index),
-    with W's weight recursion and the autotuned tile width and launch; realizations of this
-    rank only."""
+    with W's weight recursion and the autotuned tile width and launch (tuned=False: narrow tiles
+    where available, one launch per call); realizations of this rank only."""
     from paper_2011_08560_gb300 import autotune
     ens_list = ensembles or W.ensembles
     n = W.n_real
-    best = autotune.tune([(W.dim, W.L, n)] * len(ens_list)) if tuned else None
+    if tuned:
+        best = autotune.tune([(W.dim, W.L, n)] * len(ens_list))
+    else:
+        best = {"widths": {str(W.L): eamc.narrow_width(W.dim, W.L)}, "persistent": False,
+                "blocks_per_sm": 0, "sweeps_per_launch": 0}
     ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
     if best:
         autotune.prepare(ctx, best)
@@ -278,7 +287,7 @@ def run_gpu(args, rank, world):
     W = headline(args)
     S = args.sweeps_per_step
     stream = torch.cuda.Stream()
-    ctx = build_context(eamc, rank, stream.cuda_stream, W)
+    ctx = build_context(eamc, rank, stream.cuda_stream, W, tuned=not args.no_tune)
     n_chains = ctx.num_chains()
     V = W.L ** W.dim
     attempts_per_step = n_chains * V * S
@@ -795,6 +804,39 @@ def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_
     return out
 
 
+def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000):
+    """Table I analog at the headline's size, L=8, on its 1024 realizations: one density of
+    states per realization from the headline's power-law Berg iteration, shared by flat MUCA,
+    the power law (-3.6, 96) and the 1/k ensemble (each a chain of its own), and PT with the
+    paper's M = 20 on the same realizations; production with round-trip counting."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2011_08560_gb300 import eamc, scan
+    W = HEADLINE
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    res = scan.profile_scan(3, W.L, n_real, (W.alpha,), (W.pole,), seed=W.seed, dos_iters=W.iter_steps,
+                            dos_sweeps=W.iter_sweeps, prod_sweeps=prod_sweeps, recursion=eamc.EA_REC_BERG,
+                            stream=stream.cuda_stream, tile_width=eamc.narrow_width(3, W.L))
+    wall = time.perf_counter() - t0
+    pt_tau, pt_below = scan.pt_round_trips(3, W.L, n_real, PT_REPLICAS[W.L], res.e_g, seed=W.seed,
+                                           prod_sweeps=prod_sweeps, stream=stream.cuda_stream)
+    rows = {r["ensemble"]: {k: v for k, v in r.items() if k != "ensemble"} for r in res.summary()}
+    ok = np.isfinite(pt_tau)
+    rows["PT"] = {"mean_tau": float(np.mean(pt_tau[ok])) if ok.any() else None,
+                  "median_tau": float(np.median(pt_tau[ok])) if ok.any() else None,
+                  "without_rt": int((~ok).sum()), "requeued": int(pt_below.sum())}
+    return {"workload": f"3D L={W.L}, {n_real} realizations (seed {W.seed}), density of states from "
+                        f"{W.iter_steps} x {W.iter_sweeps} power-law Berg sweeps, flat / power law "
+                        f"(-3.6, 96) / 1/k chains from it, PT with M = {PT_REPLICAS[W.L]}; {prod_sweeps} "
+                        f"production sweeps each",
+            "wall_s": time.perf_counter() - t0, "muca_wall_s": wall, "ensembles": rows,
+            "table_one": res.table_one(pt_tau, pt_below), "paper_table_one": PAPER_TABLE_ONE[W.L]}
+
+
 def bench_serving(window_s: float = 10.0, drain_s: float = 30.0):
     """Serving (config 5): Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12},
     round-trip targets log-uniform in [10, 1000]; power-law MUCA with Berg's recursion; state
@@ -814,6 +856,60 @@ def bench_serving(window_s: float = 10.0, drain_s: float = 30.0):
                          f"ticks, production cap 2000 ticks (16 sweeps per tick at L=12, (12/L)^3 times "
                          f"more at smaller L)")
     return stats
+
+
+def bench_serving_saturated(n_jobs: int = 4096, window_s: float = 5.0, base: int = 16):
+    """The serving loop under saturation: n_jobs jobs of L uniform in {4..12} submitted at once
+    (long targets: all stay running), served for window_s after admission; against the plain
+    batched launch of the same chains (same tiles, same sweeps per tick).  The ratio is the
+    share of the sweep kernel's throughput the loop keeps (its per-tick control, weight steps
+    and read-backs)."""
+    import time
+
+    import torch
+
+    from paper_2011_08560_gb300 import eamc, serve
+    from paper_2011_08560_gb300.workloads import SERVING
+    Ls = SERVING["Ls"]
+    server = serve.Server(seed=SERVING["seed"], Ls=Ls, base_sweeps=base, mem_budget=8 << 30)
+    jobs = [serve.Job(jid=k, L=Ls[k % len(Ls)], rid=k, rt_target=10 ** 6, iter_steps=8, ticks_per_step=8,
+                      max_prod_ticks=10 ** 5, max_requeues=4) for k in range(n_jobs)]
+    for j in jobs:
+        server.submit(j)
+    server.step(80)                       # admission and the jobs' iteration phases
+    server.poll(wait=True)
+    a0, t0 = server.stats()["attempts"], time.perf_counter()
+    while time.perf_counter() - t0 < window_s:
+        server.step(8)
+        server.poll()
+    server.poll(wait=True)
+    t1 = time.perf_counter()
+    st = server.stats()
+    served = (st["attempts"] - a0) / ((t1 - t0) * 1e9)
+    server.close()
+    # the same chains as one batch: per L, n_jobs / 9 chains with the server's sweeps per tick
+    stream = torch.cuda.Stream()
+    ctx = eamc.Context(seed=SERVING["seed"], device=0, stream=stream.cuda_stream)
+    attempts_per_tick = 0
+    for i, L in enumerate(Ls):
+        n = sum(1 for k in range(n_jobs) if k % len(Ls) == i)
+        ctx.init_disorder(3, L, n, rid0=i * n_jobs)
+        mul = max(1, int((max(Ls) / L) ** 3 + 0.5))
+        ctx.set_sweep_multiplier(L, mul)
+        attempts_per_tick += n * L ** 3 * base * mul
+    ctx.run_sweeps(base)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.run_sweeps(base * 100)
+    e1.record(stream)
+    stream.synchronize()
+    batch = attempts_per_tick * 100 / (e0.elapsed_time(e1) * 1e6)
+    ctx.close()
+    return {"workload": f"{n_jobs} jobs, L uniform in 4..12, all running (power law, Berg), {window_s:.0f} s "
+                        f"window after admission; batch = the same chains in one muca_run_sweeps",
+            "served_attempts_per_ns": served, "batch_attempts_per_ns": batch,
+            "served_over_batch": served / batch, "ticks": st["ticks"], "lanes": st["lanes"]}
 
 
 def main():
@@ -857,6 +953,7 @@ def main():
               "uneven": bench_uneven, "serving": bench_serving,
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "recursion": bench_recursion, "small": bench_small, "flat": bench_flat_same_schedule,
+              "serving_saturated": bench_serving_saturated, "table_one_l8": bench_table_one_l8,
               "l6": bench_l6_flat_pl}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
@@ -869,9 +966,10 @@ def main():
     r = run_gpu(args, rank, world)
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = {"flat_same_schedule": bench_flat_same_schedule(), "l6_flat_pl": bench_l6_flat_pl(),
+        extras = {"table_one_l8": bench_table_one_l8(), "l6_flat_pl": bench_l6_flat_pl(),
                   "small": bench_small(), "pt": bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol(),
-                  "uneven": bench_uneven(), "serving": bench_serving(), "recursion": bench_recursion(),
+                  "uneven": bench_uneven(), "serving": bench_serving(),
+                  "serving_saturated": bench_serving_saturated(), "recursion": bench_recursion(),
                   "scan": bench_profile_scan()}
     if rank != 0:
         if world > 1:
@@ -907,6 +1005,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": r["achieved_ops"] / 1e12,
                      "peak": r["alu_peak"] / 1e12, "unit": "Tops/s",
                      "frac": r["achieved_ops"] / r["alu_peak"], "traffic": SWEEP_TRAFFIC_BYTES,
+                     "traffic_basis": "ncu dram read+write of one launch (one-time table and lattice "
+                                      "staging, independent of the sweeps per launch)",
                      "kernel": "muca_sweep_kernel<3>",
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock "

@@ -125,10 +125,13 @@ def pt_round_trips(dim: int, L: int, n_real: int, M: int, e_g, seed: int = 0, ri
 def profile_scan(dim: int, L: int, n_real: int, alphas, poles, seed: int = 0, rid0: int = 0,
                  dos_iters: int = 30, dos_sweeps: int = 2000, recursion: int = eamc.EA_REC_BERG,
                  dos_alpha: float = -3.6, dos_pole: float = 96.0, prod_sweeps: int = 20000,
-                 with_one_over_k: bool = True, stream=None) -> ScanResult:
-    """Runs the three stages above for every (alpha, Delta E) in alphas x poles."""
+                 with_one_over_k: bool = True, stream=None, tile_width: int = 32) -> ScanResult:
+    """Runs the three stages above for every (alpha, Delta E) in alphas x poles (tile_width:
+    chains per tile, see muca_set_tile_width)."""
     ctx = eamc.Context(seed=seed, stream=stream)
     try:
+        if tile_width != 32:
+            ctx.set_tile_width(L, tile_width)
         # 1. density of states (power-law target, stream 0)
         dos = ctx.init_disorder(dim, L, n_real, rid0=rid0, stream=0)
         ctx.set_ensemble(dos, n_real, eamc.EA_POWERLAW, dos_alpha, dos_pole)

@@ -392,3 +392,40 @@ def test_roundtrip_reset_and_requeue(eamc, orc):
     for k in range(n):
         assert R2[k]["n_rt"] == 0 and R2[k]["phase"] == 0 and R2[k]["requeue"] == 0
         assert R2[k]["e_min"] == E[k]
+
+
+def test_reset_chains_match_fresh_oracle_chains(eamc, orc):
+    """ea_reset_chains (a lane taking a new job) gives exactly a fresh oracle chain of the new
+    realization and stream, and leaves the other chains of the tile on their trajectories."""
+    dim, L, n = 3, 5, 40
+    ctx = eamc.Context(seed=SEED)
+    ctx.init_disorder(dim, L, n, rid0=60, stream=1)
+    ctx.set_ensemble(0, n, eamc.EA_POWERLAW, -3.6, 96.0)
+    chains = _oracle_chains(orc, dim, L, n, rid0=60, stream=1)
+    lnW = [np.zeros(c.b_top + 1) for c in chains]
+    for _ in range(2):
+        ctx.run_sweeps(30)
+        ctx.update_weights()
+        for k, c in enumerate(chains):
+            c.sweeps(30, orc.quantize(dim, lnW[k]))
+            lnW[k] = orc.update_weights(dim, L, c.parity, orc.POWERLAW, -3.6, 96.0, c.rt.e_min, lnW[k], c.hist)
+            c.hist[:] = 0
+    picked = [3, 17, 38]
+    new_rid, new_stream = [901, 902, 903], [7, 0, 5]
+    ctx.reset_chains(picked, new_rid, new_stream)
+    for k, r, s in zip(picked, new_rid, new_stream):
+        chains[k] = orc.Chain(dim, L, SEED, r, s)      # a fresh chain: flat weights, t = 0
+        lnW[k] = np.zeros(chains[k].b_top + 1)
+    desc = ctx.describe()
+    for k, r, s in zip(picked, new_rid, new_stream):
+        assert desc[k]["rid"] == r and desc[k]["stream"] == s and desc[k]["t"] == 0
+        assert desc[k]["kind"] == eamc.EA_FLAT
+    W = ctx.get_weights()
+    for k in picked:
+        assert not W[k, :chains[k].b_top + 1].any()
+    _compare_state(ctx, chains, hist=True, rt=True)
+    # every chain continues exactly (the reset ones as fresh flat chains)
+    ctx.run_sweeps(25, count_roundtrips=False)
+    for k, c in enumerate(chains):
+        c.sweeps(25, orc.quantize(dim, lnW[k]))
+    _compare_state(ctx, chains, hist=True, rt=False)

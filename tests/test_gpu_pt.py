@@ -95,19 +95,45 @@ def test_pt_errors(eamc):
 
 
 def test_pt_full_size_sampled(eamc, orc):
-    """The PT workload (L=8, 1024 realizations x 32 temperatures) at full size, with sampled
-    realizations checked against the oracle."""
+    """The PT workload (L=8, 1024 realizations x 32 temperatures) at full size: 20 sweeps, then
+    60 with round trips counted between per-realization bounds; sampled realizations checked
+    against the oracle (spins, energies, labels, per-replica round-trip records, exchange
+    counts per pair)."""
     from paper_2011_08560_gb300.workloads import PT, geometric_betas
     betas = geometric_betas(PT["M"], PT["beta_min"], PT["beta_max"])
+    n, M = PT["n_real"], PT["M"]
     ctx = eamc.Context(seed=PT["seed"])
-    ctx.pt_init(PT["dim"], PT["L"], PT["n_real"], betas)
-    ctx.pt_run(3)
+    ctx.pt_init(PT["dim"], PT["L"], n, betas)
+    ctx.pt_run(20)
+    _, E0, _, _ = ctx.pt_state(spins=False)
+    # a narrow band around the middle temperature's energy, so that round trips happen within
+    # 60 sweeps
+    e_hot = E0[:, M // 2].astype(np.int32)
+    e_g = (E0[:, M // 2] - 30).astype(np.int32)
+    ctx.pt_roundtrips(reset=True)
+    ctx.pt_set_rt_bounds(e_g, e_hot)
+    ctx.pt_run(60, count_roundtrips=True)
     S, E, lab, t = ctx.pt_state()
+    R = ctx.pt_roundtrips()
+    acc, att = ctx.pt_exchange_counts()
+    total = 0
     for rid in (0, 517, 1023):
         p = orc.PTRealization(PT["dim"], PT["L"], PT["seed"], rid, betas)
-        p.sweeps(3)
+        p.sweeps(20)
+        for k in range(M):
+            p.rt[p.label[k]] = orc.RT(phase=0, n_rt=0, t_first=-1, t_last=-1, e_min=int(p.E[k]),
+                                      e_g=0, requeue=0, pad=0)
+        p.sweeps(60, count_rt=True, e_g=int(e_g[rid]), e_hot=int(e_hot[rid]))
         assert np.array_equal(E[rid], p.E) and np.array_equal(lab[rid], p.label)
         assert np.array_equal(S[rid].reshape(-1), p.S)
+        for l in range(M):
+            want = p.rt[l].as_dict()
+            for f in ("phase", "n_rt", "t_first", "t_last", "e_min"):
+                assert R[rid][l][f] == want[f], (rid, l, f)
+            total += want["n_rt"]
+        a, tt = p.window_rates()
+        assert np.array_equal(acc[rid], a.astype(np.uint32)) and np.array_equal(att, tt)
+    assert total > 0
 
 
 def test_pt_per_realization_temperatures(eamc, orc):
