@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
     ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
-                                       "recursion", "scan", "small", "flat", "l6", "table_one_l8"],
+                                       "recursion", "scan", "small", "flat", "l6", "table_one_l8",
+                                       "paper_samples"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--no-tune", action="store_true",
@@ -837,6 +838,36 @@ def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000):
             "table_one": res.table_one(pt_tau, pt_below), "paper_table_one": PAPER_TABLE_ONE[W.L]}
 
 
+def bench_paper_samples(n_real: int = 4096, S: int = 10_000, steps: int = 3, iter_steps: int = 4,
+                        iter_sweeps: int = 2000):
+    """The headline ensemble (L=8, power law, production with frozen weights) at the paper's
+    sample count for L=8 (4000 realizations; 4096 here): a batch large enough to fill the GPU.
+    Short Berg iteration (the throughput of a production sweep does not depend on how far the
+    weights converged), autotuned tile width and launch."""
+    import dataclasses
+
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    W = dataclasses.replace(HEADLINE, n_real=n_real, iter_steps=iter_steps, iter_sweeps=iter_sweeps)
+    stream = torch.cuda.Stream()
+    ctx = build_context(eamc, 0, stream.cuda_stream, W)
+    iterate_weights(ctx, W, stream)
+    ctx.run_sweeps(S // 10, count_roundtrips=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.run_sweeps(S, count_roundtrips=True)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    launch = getattr(ctx, "tuned", None)
+    ctx.close()
+    return {"workload": f"3D L={W.L}, {n_real} realizations, power law (-3.6, 96), {steps} x {S} production "
+                        f"sweeps after {iter_steps} x {iter_sweeps} Berg iteration sweeps",
+            "attempts_per_ns": n_real * W.L ** 3 * S * steps / (ms * 1e6), "launch": launch}
+
+
 def bench_serving(window_s: float = 10.0, drain_s: float = 30.0):
     """Serving (config 5): Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12},
     round-trip targets log-uniform in [10, 1000]; power-law MUCA with Berg's recursion; state
@@ -954,6 +985,7 @@ def main():
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "recursion": bench_recursion, "small": bench_small, "flat": bench_flat_same_schedule,
               "serving_saturated": bench_serving_saturated, "table_one_l8": bench_table_one_l8,
+              "paper_samples": bench_paper_samples,
               "l6": bench_l6_flat_pl}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
@@ -966,7 +998,8 @@ def main():
     r = run_gpu(args, rank, world)
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = {"table_one_l8": bench_table_one_l8(), "l6_flat_pl": bench_l6_flat_pl(),
+        extras = {"paper_samples_l8": bench_paper_samples(), "table_one_l8": bench_table_one_l8(),
+                  "l6_flat_pl": bench_l6_flat_pl(),
                   "small": bench_small(), "pt": bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol(),
                   "uneven": bench_uneven(), "serving": bench_serving(),
                   "serving_saturated": bench_serving_saturated(), "recursion": bench_recursion(),
