@@ -8,7 +8,8 @@ arrays into it.
 
 What each function follows (Mueller, Schnabel, Janke, arXiv:2011.08560):
   energy / disorder .......... Sec. II, Eq. "hamiltonian"; 3V couplings +-1 with p = 1/2
-  muca_sweeps ................ Sec. II, Eq. "muca" (generalized Metropolis, sequential)
+  muca_sweeps ................ Sec. II, Eq. "muca" (generalized Metropolis, sequential; sites
+                               lexicographic or colour class by colour class)
   quantize ................... Eq. "muca": P_acc = min(1, W(E_new)/W(E_old)) as a u32 threshold
   ln_profile ................. Eq. "power_law" (normalised to 1 at E = 0)
   update_weights ............. Sec. II, the iterative weight procedure (W <- W P_SH / H)
@@ -88,6 +89,8 @@ def lib():
             "or_muca_sweeps": (i32, [i32, i32, u64, u32, u32, P, P, P, u64, u64, P, i32, P,
                                      P, i32, P, P]),
             "or_rt_replay": (None, [P, P, i32, i32, i32, P]),
+            "or_muca_sweeps_order": (i32, [i32, i32, u64, u32, u32, P, P, P, u64, u64, P, i32, P,
+                                           P, i32, P, P, i32]),
             "or_quantize": (None, [i32, i32, P, P]),
             "or_ln_profile": (f64, [i32, f64, f64, i32, i32]),
             "or_update_weights": (None, [i32, i32, i32, i32, i32, f64, f64, i32, P, P]),
@@ -239,8 +242,10 @@ class Chain:
 
     def __init__(self, dim: int, L: int, seed: int, rid: int, stream: int = 0,
                  J: np.ndarray | None = None, S: np.ndarray | None = None,
-                 descend_to_top: bool = True):
+                 descend_to_top: bool = True, order: int = 0):
+        """order: 0 lexicographic sweeps, 1 colour class by colour class (or_muca_sweeps_order)."""
         self.dim, self.L, self.seed, self.rid, self.stream = dim, L, seed, rid, stream
+        self.order = order
         self.V, self.nb = volume(dim, L), nbonds(dim, L)
         self.J = make_disorder(dim, L, seed, rid) if J is None else np.ascontiguousarray(J, np.int8)
         self.S = make_spins(dim, L, seed, rid, stream) if S is None else np.ascontiguousarray(S, np.int8).copy()
@@ -264,10 +269,11 @@ class Chain:
         E = np.array([self.E], dtype=np.int32)
         tr = np.zeros(n, dtype=np.int32) if trace else None
         at = np.zeros((n, self.V), dtype=np.int32) if attempt_trace else None
-        lib().or_muca_sweeps(self.dim, self.L, self.seed, self.rid, self.stream, _p(self.J),
-                             _p(self.S), _p(E), self.t, n, _p(thr), self.b_top, _p(self.hist),
-                             ctypes.byref(self.rt), int(count_rt),
-                             _p(tr) if trace else None, _p(at) if attempt_trace else None)
+        lib().or_muca_sweeps_order(self.dim, self.L, self.seed, self.rid, self.stream, _p(self.J),
+                                   _p(self.S), _p(E), self.t, n, _p(thr), self.b_top, _p(self.hist),
+                                   ctypes.byref(self.rt), int(count_rt),
+                                   _p(tr) if trace else None, _p(at) if attempt_trace else None,
+                                   self.order)
         self.E = int(E[0])
         self.t += n
         if trace and attempt_trace:

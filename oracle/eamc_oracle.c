@@ -186,23 +186,36 @@ void or_rt_replay(const int32_t *E, const int64_t *t, int n, int e_top, int e_bo
 }
 
 /* ---------------------------------------------------------------- MUCA chain */
-/* n_sweeps sweeps of single-spin-flip generalized Metropolis (Eq. "muca"), sites in
- * lexicographic order.  thr is the chain's table, thr[b*8 + n] = threshold for a move
- * from bin b at a site with n unsatisfied bonds (the move changes E by 2*(2*dim) - 4n).
- * After every attempt: e_min update, (if count_rt) one round-trip check against rt->e_g,
- * and a_trace[s*V + i] = E (if non-null).  After every sweep: hist[bin(E)] += 1 and
- * e_trace[s] = E (if non-null). */
-int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
-                   const int8_t *J, int8_t *S, int32_t *E_io, uint64_t t0, uint64_t n_sweeps,
-                   const uint32_t *thr, int b_top, uint32_t *hist, or_rt *rt, int count_rt,
-                   int32_t *e_trace, int32_t *a_trace) {
+int or_pt_colours(int L);
+int or_pt_colour(int dim, int L, int i);
+
+/* n_sweeps sweeps of single-spin-flip generalized Metropolis (Eq. "muca").  The paper fixes
+ * no order of the sites within a sweep; two orders are provided:
+ *   order 0: lexicographic (i = 0 .. V-1);
+ *   order 1: colour class by colour class (the colouring of the PT sweep, or_pt_colour: the
+ *            checkerboard for even L, three classes for odd L), each class in lexicographic
+ *            order.
+ * The random word of an attempt is keyed by its site and sweep, so it is the same in both
+ * orders.  thr is the chain's table, thr[b*8 + n] = threshold for a move from bin b at a
+ * site with n unsatisfied bonds (the move changes E by 2*(2*dim) - 4n).  After every
+ * attempt: e_min update, (if count_rt) one round-trip check against rt->e_g, and
+ * a_trace[s*V + k] = E after the k-th attempt of the sweep (if non-null).  After every sweep:
+ * hist[bin(E)] += 1 and e_trace[s] = E (if non-null). */
+int or_muca_sweeps_order(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
+                         const int8_t *J, int8_t *S, int32_t *E_io, uint64_t t0, uint64_t n_sweeps,
+                         const uint32_t *thr, int b_top, uint32_t *hist, or_rt *rt, int count_rt,
+                         int32_t *e_trace, int32_t *a_trace, int order) {
     int V = or_volume(dim, L), z = 2 * dim;
     int E = *E_io;
     int parity = ((E + or_nbonds(dim, L)) / 2) & 1;
     int e_top = or_energy_of_bin(dim, L, parity, b_top);
+    int ncol = order ? or_pt_colours(L) : 1;
     for (uint64_t s = 0; s < n_sweeps; ++s) {
         uint64_t t = t0 + s;
+        int k_att = 0;
+        for (int colour = 0; colour < ncol; ++colour)
         for (int i = 0; i < V; ++i) {
+            if (order && or_pt_colour(dim, L, i) != colour) continue;
             int x = i % L, row = i / L;            /* row = y (+ L z) */
             uint32_t r = rand_word(seed, (uint32_t)(4 * row + (x >> 2)), (uint32_t)t, rid,
                                    0u | (stream << 8), x & 3);
@@ -215,7 +228,8 @@ int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
             if (accept) { S[i] = (int8_t)-S[i]; E += dE; }
             if (E < rt->e_min) rt->e_min = E;
             if (count_rt) rt_check(rt, E, e_top, rt->e_g, t);
-            if (a_trace) a_trace[(size_t)s * V + i] = E;
+            if (a_trace) a_trace[(size_t)s * V + k_att] = E;
+            ++k_att;
         }
         hist[or_bin_of_energy(dim, L, E)] += 1;
         if (e_trace) e_trace[s] = E;
@@ -223,6 +237,15 @@ int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
     if (count_rt && rt->e_min < rt->e_g) rt->requeue = 1;
     *E_io = E;
     return 0;
+}
+
+/* the lexicographic order (order 0) */
+int or_muca_sweeps(int dim, int L, uint64_t seed, uint32_t rid, uint32_t stream,
+                   const int8_t *J, int8_t *S, int32_t *E_io, uint64_t t0, uint64_t n_sweeps,
+                   const uint32_t *thr, int b_top, uint32_t *hist, or_rt *rt, int count_rt,
+                   int32_t *e_trace, int32_t *a_trace) {
+    return or_muca_sweeps_order(dim, L, seed, rid, stream, J, S, E_io, t0, n_sweeps, thr, b_top,
+                                hist, rt, count_rt, e_trace, a_trace, 0);
 }
 
 /* ---------------------------------------------------------------- weights */

@@ -1,0 +1,103 @@
+"""Pins of the oracle's second sweep order: colour class by colour class (the PT colouring:
+the checkerboard for even L, three classes for odd L), each class in lexicographic order.
+
+The paper fixes no order of the single-spin-flip attempts within a sweep; any fixed order of
+updates that each satisfy detailed balance samples the same ensemble.  So the pins of the
+lexicographic order (exact histograms from the enumerated density of states, the canonical
+special case, incremental energy, resume) must hold for this order too, and the order itself
+is pinned by what sets it apart: within a colour pass no two attempted sites are neighbours,
+so every attempt's energy change is the one its site had when the pass began.
+"""
+import numpy as np
+import pytest
+
+from tests.test_oracle_pins import _exact_lnomega_bins, _exact_mean_energy, _weights_from
+
+
+@pytest.mark.parametrize("dim,L,rid", [(2, 4, 1), (3, 3, 2)])
+def test_flat_histogram_with_exact_weights(orc, dim, L, rid):
+    seed = 21
+    J = orc.make_disorder(dim, L, seed, rid)
+    lnO, par, bt = _exact_lnomega_bins(orc, dim, L, J)
+    ch = orc.Chain(dim, L, seed, rid, J=J, order=1)
+    ch.sweeps(400_000 if dim == 2 else 60_000, orc.quantize(dim, _weights_from(-lnO)))
+    reach = np.isfinite(lnO)
+    rel = ch.hist[reach].astype(np.float64)
+    rel = rel / rel.mean() - 1.0
+    assert np.abs(rel).max() < 0.12 and np.abs(rel).mean() < 0.05, rel
+
+
+def test_power_law_histogram_follows_profile(orc):
+    dim, L, seed, rid = 2, 4, 21, 1
+    J = orc.make_disorder(dim, L, seed, rid)
+    lnO, par, bt = _exact_lnomega_bins(orc, dim, L, J)
+    reach = np.isfinite(lnO)
+    eg = orc.energy_of_bin(dim, L, par, int(np.argmax(reach)))
+    lnP = np.array([orc.ln_profile(1, -3.6, 8.0, eg, orc.energy_of_bin(dim, L, par, b)) for b in range(bt + 1)])
+    ch = orc.Chain(dim, L, seed, rid, J=J, order=1)
+    ch.sweeps(400_000, orc.quantize(dim, _weights_from(lnP - lnO)))
+    h = ch.hist[reach].astype(np.float64)
+    p = np.exp(lnP[reach])
+    ratio = (h / h.sum()) / (p / p.sum())
+    assert np.abs(ratio - 1.0).max() < 0.12, ratio
+
+
+def test_canonical_special_case(orc):
+    dim, L, seed, rid = 2, 4, 3, 4
+    J = orc.make_disorder(dim, L, seed, rid)
+    g = orc.dos_bruteforce(dim, L, J)
+    par = orc.parity(dim, L, J)
+    bt = orc.btop(dim, L, par)
+    lnW = orc.build_weights(dim, L, par, orc.CANON, 0.0, 0.0, 0.6, 0, np.zeros(bt + 1))
+    ch = orc.Chain(dim, L, seed, rid, J=J, order=1)
+    thr = orc.quantize(dim, lnW)
+    ch.sweeps(2000, thr)
+    means = [ch.sweeps(10_000, thr, trace=True).mean() for _ in range(20)]
+    m, se = np.mean(means), np.std(means, ddof=1) / np.sqrt(len(means))
+    exact = _exact_mean_energy(g, 32, 0.6, emax=orc.energy_of_bin(dim, L, par, bt))
+    assert abs(m - exact) < 5 * se + 0.02, (m, exact, se)
+
+
+@pytest.mark.parametrize("dim,L", [(3, 4), (3, 5), (2, 6)])
+def test_incremental_energy_and_resume(orc, dim, L):
+    a = orc.Chain(dim, L, 1, 0, order=1)
+    b = orc.Chain(dim, L, 1, 0, order=1)
+    rng = np.random.default_rng(1)
+    thr = orc.quantize(dim, -0.05 * rng.standard_normal(a.b_top + 1).cumsum())
+    ta = a.sweeps(40, thr, trace=True)
+    tb = np.concatenate([b.sweeps(15, thr, trace=True), b.sweeps(25, thr, trace=True)])
+    assert np.array_equal(ta, tb) and np.array_equal(a.S, b.S) and np.array_equal(a.hist, b.hist)
+    assert a.E == orc.energy(dim, L, a.J, a.S) and a.E <= a.e_top
+
+
+@pytest.mark.parametrize("dim,L", [(3, 4), (3, 5), (2, 5)])
+def test_colour_pass_energy_changes_are_those_of_the_pass_start(orc, dim, L):
+    """Attempts in the first colour pass of a sweep change E by 0 (rejected) or by the change
+    flipping that site would have caused in the configuration the pass began with; the
+    attempts visit the colour's sites in lexicographic order.  The lexicographic order fails
+    this (a site's field changes when a neighbour flipped earlier in the sweep)."""
+    seed, rid = 6, 3
+    rng = np.random.default_rng(L)
+    col = np.array([orc.pt_colour(dim, L, i) for i in range(L ** dim)])
+    sites0 = np.nonzero(col == 0)[0]
+    found_difference = False
+    for order in (1, 0):
+        ch = orc.Chain(dim, L, seed, rid, order=order)
+        thr = orc.quantize(dim, -0.1 * rng.standard_normal(ch.b_top + 1).cumsum())
+        S0, E0 = ch.S.copy(), ch.E
+        at = ch.sweeps(1, thr, attempt_trace=True)[0]
+        dE_seen = np.diff(np.concatenate([[E0], at]))
+        visited = sites0 if order == 1 else np.arange(L ** dim)[: len(sites0)]
+        ok = True
+        for k, i in enumerate(visited):
+            S1 = S0.copy()
+            S1[i] = -S1[i]
+            want = orc.energy(dim, L, ch.J, S1) - E0
+            if not (dE_seen[k] == 0 or dE_seen[k] == want):
+                ok = False
+        if order == 1:
+            assert ok
+            assert (dE_seen[: len(sites0)] != 0).sum() > 0          # some attempts accepted
+        else:
+            found_difference = found_difference or not ok
+    assert found_difference or dim == 2
