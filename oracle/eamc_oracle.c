@@ -25,6 +25,10 @@
  *                  initial spins (i>>2, 0, rid, 2 | stream<<8) word i&3
  *                  MUCA update   (4*row + x/4, t, rid, 0 | stream<<8) word x&3, where
  *                                row = y (+ L z) is the site's lattice row along x
+ *                  MUCA update in the colour order
+ *                                (4*row + j/4, t, rid, (5 + c) | stream<<8) word j&3, where
+ *                                c is the site's colour and j its rank among the colour-c
+ *                                sites of its row (in x order)
  *                  PT update     (8*i + m/4, t, rid>>5, 4 | slot<<8) word m&3,
  *                                32 words whose bit (rid&31) gives bit 31-m of r
  *                  PT swap       (k, t, rid, 1) word 0
@@ -195,8 +199,9 @@ int or_pt_colour(int dim, int L, int i);
  *   order 1: colour class by colour class (the colouring of the PT sweep, or_pt_colour: the
  *            checkerboard for even L, three classes for odd L), each class in lexicographic
  *            order.
- * The random word of an attempt is keyed by its site and sweep, so it is the same in both
- * orders.  thr is the chain's table, thr[b*8 + n] = threshold for a move from bin b at a
+ * The random word of an attempt is keyed by its site and sweep; the colour order draws from
+ * its own streams (tags 5 + colour), numbered by the site's rank within the colour-c sites of
+ * its row, so that a row's colour-c attempts take consecutive words.  thr is the chain's table, thr[b*8 + n] = threshold for a move from bin b at a
  * site with n unsatisfied bonds (the move changes E by 2*(2*dim) - 4n).  After every
  * attempt: e_min update, (if count_rt) one round-trip check against rt->e_g, and
  * a_trace[s*V + k] = E after the k-th attempt of the sweep (if non-null).  After every sweep:
@@ -217,8 +222,16 @@ int or_muca_sweeps_order(int dim, int L, uint64_t seed, uint32_t rid, uint32_t s
         for (int i = 0; i < V; ++i) {
             if (order && or_pt_colour(dim, L, i) != colour) continue;
             int x = i % L, row = i / L;            /* row = y (+ L z) */
-            uint32_t r = rand_word(seed, (uint32_t)(4 * row + (x >> 2)), (uint32_t)t, rid,
-                                   0u | (stream << 8), x & 3);
+            uint32_t r;
+            if (order) {
+                int j = 0;                             /* rank among the row's colour-c sites */
+                for (int x2 = 0; x2 < x; ++x2) j += or_pt_colour(dim, L, row * L + x2) == colour;
+                r = rand_word(seed, (uint32_t)(4 * row + (j >> 2)), (uint32_t)t, rid,
+                              (uint32_t)(5 + colour) | (stream << 8), j & 3);
+            } else {
+                r = rand_word(seed, (uint32_t)(4 * row + (x >> 2)), (uint32_t)t, rid,
+                              0u | (stream << 8), x & 3);
+            }
             int h = local_field(dim, L, J, S, i);
             int n_unsat = (z - S[i] * h) / 2;        /* S_i h_i = #sat - #unsat */
             int dE = 2 * S[i] * h;                    /* = 2z - 4 n_unsat */

@@ -101,3 +101,46 @@ def test_colour_pass_energy_changes_are_those_of_the_pass_start(orc, dim, L):
         else:
             found_difference = found_difference or not ok
     assert found_difference or dim == 2
+
+
+def _unsat(dim, L, J, S, i):
+    """unsatisfied bonds at site i (bond (i, d) joins i and i + e_d, coupling J[i*dim + d])"""
+    co = [(i // L ** d) % L for d in range(dim)]
+    n = 0
+    for d in range(dim):
+        for sgn in (1, -1):
+            c2 = list(co)
+            c2[d] = (c2[d] + sgn) % L
+            j = sum(c2[e] * L ** e for e in range(dim))
+            jb = J[(i if sgn == 1 else j) * dim + d]
+            n += int(jb * S[i] * S[j] < 0)
+    return n
+
+
+@pytest.mark.parametrize("dim,L,stream", [(2, 4, 0), (3, 4, 3), (3, 3, 1), (2, 5, 2)])
+def test_colour_order_random_stream(orc, dim, L, stream):
+    """The colour order's random words: the j-th colour-c site of a row takes word j&3 of
+    Philox call (4 row + j/4, t, rid, (5 + c) | stream<<8).  Pinned on the zero-energy moves:
+    with acceptance 1/2 for class n = dim (no change of E) and 0 for every other class, a sweep
+    flips exactly the sites that have dim unsatisfied bonds when reached and whose word is below
+    2^31, colour class by colour class.  The words come from the Philox known-answer-pinned
+    primitive."""
+    seed, rid = 0x1234_5678_9ABC, 7
+    ch = orc.Chain(dim, L, seed, rid, stream, order=1)
+    thr = np.zeros((ch.b_top + 1) * 8, dtype=np.uint32)
+    thr[dim::8] = 1 << 31
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    S = ch.S.copy()
+    E0 = ch.E
+    for t in range(2):
+        for colour in range(orc.pt_colours(L)):
+            for row in range(ch.V // L):
+                sites = [row * L + x for x in range(L) if orc.pt_colour(dim, L, row * L + x) == colour]
+                for j, i in enumerate(sites):
+                    w = orc.philox([4 * row + j // 4, t, rid, (5 + colour) | (stream << 8)], key)[j & 3]
+                    if _unsat(dim, L, ch.J, S, i) == dim and w < (1 << 31):
+                        S[i] = -S[i]
+    ch.sweeps(2, thr)
+    assert ch.E == E0
+    assert np.array_equal(ch.S, S)
+    assert (S != orc.Chain(dim, L, seed, rid, stream).S).any()   # some sites flipped
