@@ -144,6 +144,30 @@ int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
  * sweeps (0 = one launch).  Results do not depend on any of these settings. */
 int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch, int blocks_per_sm);
 
+/* sweep orders (muca_set_sweep_order) */
+#define EA_ORDER_LEX 0     /* sites in lexicographic order */
+#define EA_ORDER_COLOUR 1  /* colour class by colour class, each class in lexicographic order */
+
+/* a2 -- the order of the attempts within a sweep for every chain of the context (the paper fixes
+ * none; any fixed order samples the same ensemble, but trajectories differ):
+ *   EA_ORDER_LEX (default): i = 0 .. V-1; random word of site (x, row): word x&3 of Philox call
+ *   (4 row + x/4, t, rid, stream << 8);
+ *   EA_ORDER_COLOUR: the colour classes of the PT sweep one after the other (the checkerboard,
+ *   even coordinate sum first, for even L; for odd L colour (c(x)+c(y)+c(z)) mod 3 with
+ *   c(x) = x mod 3 except c(L-1) = 1 when L = 1 (mod 3)), each in lexicographic order; the
+ *   j-th colour-c site of a row takes word j&3 of call (4 row + j/4, t, rid, (5 + c) | stream << 8).
+ *   No two sites of a class are neighbours, so each attempt's class is fixed when its class
+ *   begins.  Even L runs one lane per chain in the tiles of the lexicographic kernel (the tile
+ *   widths of muca_set_tile_width apply) and needs one candidate-threshold pair per attempt
+ *   instead of two classes' worth: the faster order for even L up to 8.  Odd L runs one warp per
+ *   chain, resolving the attempts of a pass four at a time from acceptance ballots over the
+ *   reachable bins.
+ * chains_per_cta (colour order, odd L only): warps (chains) per thread block, 1, 2, 4 or 8, or 0
+ * to choose per launch (the largest that still gives every SM a block).  Applies from the next
+ * muca_run_sweeps or graph capture; the order is not part of a snapshot.  EA_EINVAL for an
+ * unknown order or count. */
+int muca_set_sweep_order(ea_ctx *ctx, int order, int chains_per_cta);
+
 /* a8 -- chains per tile for chains of linear size L added afterwards (ea_init_disorder):
  * width 32 (the default, every L) or 16 (3D, L = 7, 8).  A tile is one
  * warp; with width W < 32 each of its W chains runs on 32/W lanes side by side, so the tile needs

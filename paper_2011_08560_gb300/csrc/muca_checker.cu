@@ -1,0 +1,485 @@
+// muca_checker.cu -- a2 + a3 in the colour order for even L (the checkerboard): the
+// multicanonical sweep (Sec. II, Eq. "muca") with the sites of a sweep taken colour by colour,
+// each colour in lexicographic order, for 32 (or 16) independent chains per tile, one lane per
+// chain.
+//
+// In a colour pass no two attempted sites are neighbours, so the class n of every attempt
+// (unsatisfied bonds, the move changes the bin by dim - n) is fixed when the pass begins.  The
+// only sequential coupling of a chain's attempts is its energy bin: attempt i+1's threshold is
+// thr[b][n_{i+1}] with b = b_i or b_i + dim - n_i, so both candidates are loaded before
+// attempt i is decided and the decision only selects.  That leaves one class extraction, two
+// loads, two selects and a compare per attempt on the consumer warp (the lexicographic order
+// has to carry two candidate classes as well, because consecutive sites are neighbours).
+//
+// Eight warps; warp w issues on scheduler w % 4, and each scheduler has one busy role: 0 the
+// consumer; 1 and 5 the classes of the first and second half of a record's rows; 3 and 7 their
+// random words; 2 the measurement (lowest energy, round trips, histogram), one record behind the
+// consumer; 4 and 6 only take part in the barriers.  A record is RPR consecutive rows of one pass
+// (four where the row count allows it and L <= 8, else two): the colour-c sites of
+// those rows, RPR L / 2 attempts, with each attempt's class as its table offset n * NSB (16
+// bits) and its random word.  The consumer leaves the bin after every attempt for the
+// measurement.  Within a pass the producers may run any number of records ahead (the classes
+// read only the other colour's spins and each site's own spin, which its own record changes), so
+// they run LAG records ahead; at the start of a pass one extra barrier lets them refill, because
+// the first plane's classes read the last plane of the previous pass.
+//
+// Random words (the colour-order streams): the j-th colour-c site of row r takes word j&3 of
+// Philox call (4 r + j/4, t, rid, (5 + c) | stream << 8).
+//
+// Lattice layout as in the lexicographic kernel: row words with one nibble per site (bit 0
+// used), chain-interleaved; thresholds lane-interleaved in shared memory when they fit, else
+// read through L1.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "eamc_internal.cuh"
+
+namespace eamc {
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kCkWarps = 8;
+constexpr int kCkMeasure = 2;
+constexpr int kCkThreads = 32 * kCkWarps;
+// warp roles: classes of row h of a record (warps 1, 5), random words of row h (warps 3, 7)
+__device__ __forceinline__ bool ck_classes(int warp) { return warp == 1 || warp == 5; }
+__device__ __forceinline__ bool ck_random(int warp) { return warp == 3 || warp == 7; }
+
+template <int L>
+using CkRow = typename std::conditional<(L <= 8), uint32_t, uint64_t>::type;
+
+template <class T, int L>
+__device__ __forceinline__ T ck_mask() {
+    return (4 * L == 8 * (int)sizeof(T)) ? ~T(0) : ((T(1) << (4 * L)) - 1);
+}
+
+// nibble x <- nibble x+1 (mod L), and nibble x <- nibble x-1
+template <class T, int L>
+__device__ __forceinline__ T ck_next(T r) {
+    return ((r >> 4) | (r << (4 * L - 4))) & ck_mask<T, L>();
+}
+template <class T, int L>
+__device__ __forceinline__ T ck_prev(T r) {
+    return ((r << 4) | (r >> (4 * L - 4))) & ck_mask<T, L>();
+}
+
+template <int DIM, int L, int W>
+struct CkGeo {
+    static_assert((L & 1) == 0, "the checkerboard needs even L");
+    static_assert(W == 32 || W == 16, "tile width");
+    using T = CkRow<L>;
+    static constexpr int NR = DIM == 3 ? L * L : L;  // rows along x (even)
+    static constexpr int V = NR * L;
+    static constexpr int B = ((DIM * V) / 2 >> 1) + 1;
+    static constexpr int HALF = L / 2;              // colour sites per row
+    static constexpr int NGC = (HALF + 3) / 4;      // Philox calls per row and pass
+    static constexpr int RPR = (NR % 4 == 0 && L <= 8) ? 4 : 2;  // rows per record
+    static constexpr int NA = RPR * HALF;           // attempts per record
+    static constexpr int NP = NR / RPR;             // records per pass
+    static constexpr int OW = (HALF + 1) / 2;       // 32-bit words of 16-bit class offsets per row
+    static constexpr int OFFQ = (RPR * OW + 3) / 4; // uint4 slots of class offsets (row h at word h * OW)
+    static constexpr int HQ = OFFQ + RPR * NGC;     // uint4 slots per lane per record
+    static constexpr int LAG = NP >= 3 ? 2 : 1;     // records the producers run ahead
+    // ring of records, indexed by the record count over the whole launch: record g is read by
+    // the consumer after barrier g (and preloaded after g-1) while record g+LAG is written; one
+    // buffer more than that needs (measured faster)
+    static constexpr int NBUF = LAG + 2;
+    static constexpr int FIELDS = DIM + 1;          // S, Jx, Jy, (Jz)
+    static constexpr size_t LATTICE_BYTES = (size_t)FIELDS * NR * W * sizeof(T);
+    static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * W * 16;
+    static constexpr size_t RES_BYTES = (size_t)2 * NA * W * sizeof(int);  // bin row offset after each attempt, two records
+    static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * W * sizeof(uint32_t);
+    static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES;
+    static constexpr bool SMEM_THR = BASE_BYTES + THR_BYTES <= 225 * 1024;
+    static constexpr size_t SMEM = BASE_BYTES + (SMEM_THR ? THR_BYTES : 0);
+};
+
+template <bool SMEM>
+__device__ __forceinline__ uint32_t ck_thr(const char *p) {
+    if constexpr (SMEM) return *reinterpret_cast<const uint32_t *>(p);
+    else return __ldg(reinterpret_cast<const uint32_t *>(p));
+}
+
+template <int DIM, int L, int W>
+__device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotState *__restrict__ slots,
+                                             uint32_t *__restrict__ spins, const uint32_t *__restrict__ bonds,
+                                             const uint32_t *__restrict__ thr, uint32_t *__restrict__ hist,
+                                             uint64_t n_sweeps, PhiloxKey key, int count_rt,
+                                             unsigned *__restrict__ diag, unsigned char *smem_raw) {
+    using G = CkGeo<DIM, L, W>;
+    using T = typename G::T;
+    constexpr int NR = G::NR, NP = G::NP, HALF = G::HALF, NGC = G::NGC, LAG = G::LAG, NBUF = G::NBUF;
+    constexpr int RPR = G::RPR, NA = G::NA;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ln = lane & (W - 1);  // chain of this lane; lanes ln + W, ... mirror it
+    const bool owner = lane < W;
+
+    T *Rs = reinterpret_cast<T *>(smem_raw);  // spins, nibble x = 1 if S = -1
+    T *JXs = Rs + NR * W;                     // bond (x, x+1) has J = -1
+    T *JYs = Rs + 2 * NR * W;                 // bond (y, y+1)
+    T *JZs = Rs + 3 * NR * W;                 // bond (z, z+1)  (DIM == 3)
+    uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
+    int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2 records][NA][W]
+    const uint32_t *gsp = spins + td.spin_off;
+    const uint32_t *gbd = bonds + td.bond_off;
+    for (int row = warp; row < NR; row += kCkWarps) {
+        T r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            const int i = row * L + x;
+            r |= T((gsp[i] >> ln) & 1u) << (4 * x);
+            jx |= T((gbd[i * DIM + 0] >> ln) & 1u) << (4 * x);
+            jy |= T((gbd[i * DIM + 1] >> ln) & 1u) << (4 * x);
+            if constexpr (DIM == 3) jz |= T((gbd[i * DIM + 2] >> ln) & 1u) << (4 * x);
+        }
+        Rs[row * W + ln] = r;
+        JXs[row * W + ln] = jx;
+        JYs[row * W + ln] = jy;
+        if constexpr (DIM == 3) JZs[row * W + ln] = jz;
+    }
+
+    const int slot = tile * kTile + ln;
+    SlotState ss = slots[slot];
+    const bool active = ss.active != 0;
+    const uint64_t lrow = td.w_base + (uint64_t)ln * G::B;
+    // element (b, n) of this chain's table at byte offset b * RSB + n * NSB from `tab`; rows
+    // -DIM .. B-1+DIM are addressable (zero padding), so a candidate row one move away from a
+    // valid row needs no clamp
+    constexpr int NSB = G::SMEM_THR ? 4 * W : 4;
+    constexpr int RSB = 8 * NSB;
+    const char *tab;
+    if constexpr (G::SMEM_THR) {
+        uint32_t *TH = reinterpret_cast<uint32_t *>(smem_raw + G::BASE_BYTES);
+        if (warp == 1) {
+            constexpr int NM = 32 / W;
+            const int mi = lane / W;
+            const uint4 *src = reinterpret_cast<const uint4 *>(thr + lrow * 8);
+            for (int b = mi; b < G::B; b += NM) {
+                const uint4 a = src[2 * b], c = src[2 * b + 1];
+                uint32_t *d = TH + (b + DIM) * 8 * W + ln;
+                d[0] = a.x; d[W] = a.y; d[2 * W] = a.z; d[3 * W] = a.w;
+                d[4 * W] = c.x; d[5 * W] = c.y; d[6 * W] = c.z; d[7 * W] = c.w;
+            }
+            for (int k = mi; k < DIM * 8; k += NM) {
+                TH[k * W + ln] = 0u;
+                TH[((G::B + DIM) * 8 + k) * W + ln] = 0u;
+            }
+        }
+        tab = reinterpret_cast<const char *>(TH + DIM * 8 * W + ln);
+    } else {
+        tab = reinterpret_cast<const char *>(thr + lrow * 8);
+    }
+    const uint64_t t0 = ss.t;
+    const uint64_t n_pass = n_sweeps * 2;  // colour passes
+
+    __syncthreads();
+    // Every warp passes the same barriers: one after staging, per pass one fill barrier and NP
+    // record barriers, one at the end.
+    if (warp >= 1) {
+        // ---- producers: record p of colour pass c (sweep t) into ring buffer k
+        auto produce = [&](int c, int p, uint32_t t, int k) {
+            uint4 *buf = hand + k * G::HQ * W;
+            const int r0 = RPR * p;
+            const int h0 = warp >= 4 ? RPR / 2 : 0;  // this warp prepares rows h0 .. h0 + RPR/2 - 1 of the record
+            if (ck_random(warp)) {  // clamped as in the lexicographic kernel
+                const uint32_t c3 = (uint32_t)(5 + c) | (ss.stream << 8);
+#pragma unroll
+                for (int h = h0; h < h0 + RPR / 2; ++h) {
+                    const int r = r0 + h;
+#pragma unroll
+                    for (int g = 0; g < NGC; ++g) {
+                        uint4 w = philox4x32_10(make_uint4((uint32_t)(4 * r + g), t, ss.rid, c3), key);
+                        w.x = active ? min(w.x, kAlways - 1u) : kAlways;
+                        w.y = active ? min(w.y, kAlways - 1u) : kAlways;
+                        w.z = active ? min(w.z, kAlways - 1u) : kAlways;
+                        w.w = active ? min(w.w, kAlways - 1u) : kAlways;
+                        buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
+                    }
+                }
+                return;
+            }
+            // classes of row h (nibble 2j of s: the j-th colour site), stored as table offsets
+            // n * NSB, 16 bits per attempt, the row's offsets from word h * OW
+#pragma unroll
+            for (int h = h0; h < h0 + RPR / 2; ++h) {
+            T s;
+            {
+                const int r = r0 + h, y = r % L, z = DIM == 3 ? r / L : 0;
+                const T R = Rs[r * W + ln];
+                const T uxp = R ^ ck_next<T, L>(R) ^ JXs[r * W + ln];
+                const int ryp = (y == L - 1) ? r - (L - 1) : r + 1;
+                const int rym = (y == 0) ? r + (L - 1) : r - 1;
+                T sum = uxp + ck_prev<T, L>(uxp) + (R ^ Rs[ryp * W + ln] ^ JYs[r * W + ln]) +
+                        (R ^ Rs[rym * W + ln] ^ JYs[rym * W + ln]);
+                if constexpr (DIM == 3) {
+                    const int rzp = (z == L - 1) ? r - (L - 1) * L : r + L;
+                    const int rzm = (z == 0) ? r + (L - 1) * L : r - L;
+                    sum += (R ^ Rs[rzp * W + ln] ^ JZs[r * W + ln]) + (R ^ Rs[rzm * W + ln] ^ JZs[rzm * W + ln]);
+                }
+                const int x0 = (c + y + z) & 1;  // first colour-c site of the row
+                s = sum >> (4 * x0);
+            }
+            uint32_t off[G::OW];
+#pragma unroll
+            for (int q = 0; q < G::OW; ++q) off[q] = 0u;
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+                const uint32_t n = (uint32_t)((s >> (8 * j)) & 0xF);
+                off[j >> 1] |= (n * NSB) << (16 * (j & 1));
+            }
+#pragma unroll
+            for (int q = 0; q < G::OW; ++q) {
+                const int wd = h * G::OW + q;
+                reinterpret_cast<uint32_t *>(buf + (wd >> 2) * W + ln)[wd & 3] = off[q];
+            }
+            }
+        };
+        const bool producer = ck_classes(warp) || ck_random(warp);
+        // ---- measurement, one record behind the consumer
+        int phase = ss.phase, nrt = ss.n_rt;
+        int64_t tf = ss.t_first, tl = ss.t_last;
+        const int topB = ss.b_top * RSB, botB = ss.b_g * RSB;
+        int pmin = ss.b_min * RSB, pnow = ss.b * RSB;
+        bool out_of_range = false;
+        uint64_t mrec = 0;  // records measured
+        auto measure = [&](uint64_t gm) {  // record gm: the bin row offset after each of its attempts
+            const int *r = res + (int)(gm & 1) * NA * W + ln;
+            int lo = 0x7FFFFFFF, hi = -0x7FFFFFFF;
+            uint32_t mtop = 0u, mbot = 0u;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int pr = r[a * W];
+                lo = min(lo, pr);
+                hi = max(hi, pr);
+                mtop |= (uint32_t)(pr >= topB) << a;
+                mbot |= (uint32_t)(pr <= botB) << a;
+                if (a == NA - 1) pnow = pr;
+            }
+            pmin = min(pmin, lo);
+            out_of_range |= (lo < 0) | (hi > topB);
+            const uint64_t sweep = mrec / (2 * NP);
+            if (count_rt && active && ((phase == 1) ? mbot : mtop) != 0u) {
+                const int64_t t = (int64_t)(t0 + sweep);
+                int a0 = 0;
+                while (a0 < NA) {
+                    const uint32_t m = ((phase == 1) ? mbot : mtop) >> a0;
+                    if (m == 0u) break;
+                    a0 += __ffs(m);
+                    if (phase == 0) { tf = t; phase = 1; }
+                    else if (phase == 1) { phase = 2; }
+                    else { nrt += 1; tl = t; phase = 1; }
+                }
+            }
+            if (++mrec % (2 * NP) == 0 && active && owner) atomicAdd(&hist[lrow + pnow / RSB], 1u);
+        };
+        uint64_t g = 0;  // records the consumer has been given
+        for (uint64_t q = 0; q < n_pass; ++q) {
+            const int c = (int)(q & 1);
+            const uint32_t t = (uint32_t)(t0 + (q >> 1));
+            __syncthreads();  // fill barrier: the previous pass is complete
+            if (warp == kCkMeasure && g > 0) measure(g - 1);
+            if (producer)
+                for (int p = 0; p < LAG; ++p) produce(c, p, t, (int)((g + p) % NBUF));
+            for (int k = 0; k < NP; ++k) {
+                __syncthreads();  // record barrier k: records .. k+LAG-1 complete, consumer done with k-1
+                if (producer && k + LAG < NP) produce(c, k + LAG, t, (int)((g + LAG) % NBUF));
+                if (warp == kCkMeasure && k > 0) measure(g - 1);
+                ++g;
+            }
+        }
+        __syncthreads();
+        if (warp == kCkMeasure) {
+            if (g > 0) measure(g - 1);
+            ss.b = pnow / RSB;
+            ss.b_min = pmin / RSB;
+            ss.phase = phase;
+            ss.n_rt = nrt;
+            ss.t_first = tf;
+            ss.t_last = tl;
+            ss.t = t0 + n_sweeps;
+            if (count_rt && active && energy_of_bin(DIM * G::V, ss.parity, ss.b_min) < ss.e_g) ss.requeue = 1;
+            if (owner) slots[slot] = ss;
+            if (diag && __any_sync(kFull, active && out_of_range) && lane == 0) atomicOr(diag, 1u);
+        }
+        return;
+    }
+
+    // ---- consumer
+    // the previous attempt, applied lazily: row offset it was evaluated at (rq), offset change if
+    // it was accepted (dq) and whether it was (pa)
+    int rq = ss.b * RSB, dq = 0;
+    bool pa = false;
+    uint32_t thA = 0u, thB = 0u;  // candidate thresholds of the next attempt (previous rejected / accepted)
+    uint4 noff[G::OFFQ], nrr[RPR * NGC];  // the next record (read one barrier early)
+    auto load_rec = [&](uint64_t gk) {
+        const uint4 *buf = hand + (int)(gk % NBUF) * G::HQ * W;
+#pragma unroll
+        for (int q = 0; q < G::OFFQ; ++q) noff[q] = buf[q * W + ln];
+#pragma unroll
+        for (int i = 0; i < RPR * NGC; ++i) nrr[i] = buf[(G::OFFQ + i) * W + ln];
+    };
+    uint64_t g = 0;
+    for (uint64_t q = 0; q < n_pass; ++q) {
+        const int c = (int)(q & 1);
+        __syncthreads();  // fill barrier
+        bool have_next = false;
+        for (int k = 0; k < NP; ++k, ++g) {
+            __syncthreads();  // record barrier k
+            if (LAG == 1 || k == 0) load_rec(g);
+            uint32_t off[4 * G::OFFQ];  // 16-bit class offset of attempt (h, j) at bits 16 (j & 1) of off[h OW + j / 2]
+#pragma unroll
+            for (int q = 0; q < G::OFFQ; ++q) {
+                off[4 * q] = noff[q].x; off[4 * q + 1] = noff[q].y; off[4 * q + 2] = noff[q].z; off[4 * q + 3] = noff[q].w;
+            }
+            uint4 rr[RPR * NGC];
+#pragma unroll
+            for (int i = 0; i < RPR * NGC; ++i) rr[i] = nrr[i];
+            const bool more = k + 1 < NP;  // a next record in this pass
+            if (LAG >= 2 && more) load_rec(g + 1);
+            const int r0 = RPR * k;
+            int on = (int)(off[0] & 0xFFFFu);  // this attempt's class offset
+            if (!have_next) {
+                thA = ck_thr<G::SMEM_THR>(tab + rq + on);
+                thB = ck_thr<G::SMEM_THR>(tab + rq + dq + on);
+            }
+            have_next = false;
+            int *resb = res + (int)(g & 1) * NA * W + ln;
+            T flipped[RPR];  // bit 8j: the j-th colour site of the row flipped
+#pragma unroll
+            for (int h = 0; h < RPR; ++h) flipped[h] = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int h = a / HALF, j = a % HALF;
+                // the next attempt's class offset: this record's, or the next record's first
+                int off1 = 0;
+                bool next = true;
+                if (a + 1 < NA) {
+                    const int h1 = (a + 1) / HALF, j1 = (a + 1) % HALF, wd = h1 * G::OW + (j1 >> 1);
+                    off1 = (int)((off[wd] >> (16 * (j1 & 1))) & 0xFFFFu);
+                } else if (LAG >= 2 && more) {
+                    off1 = (int)(noff[0].x & 0xFFFFu);
+                    have_next = true;
+                } else {
+                    next = false;
+                }
+                const int dx = DIM * RSB - 8 * on;  // bin change if accepted: (dim - n) rows
+                const int rB = rq + dq;
+                // all four candidate addresses first; the previous decision only selects.  The
+                // next attempt's loads are issued before this attempt's threshold is used, so that
+                // their latency overlaps this decision (a warp issues in order)
+                const int aA0 = rq + off1, aA1 = rB + off1, aB0 = aA0 + dx, aB1 = aA1 + dx;
+                uint32_t nA = 0u, nB = 0u;
+                if (next) {
+                    nA = ck_thr<G::SMEM_THR>(tab + (pa ? aA1 : aA0));
+                    nB = ck_thr<G::SMEM_THR>(tab + (pa ? aB1 : aB0));
+                }
+                const uint32_t th = pa ? thB : thA;
+                const int rx = pa ? rB : rq;
+                const uint32_t r = uint4_get(rr[h * NGC + (j >> 2)], j & 3);
+                const bool acc = r < th;  // r clamped by the producer
+                flipped[h] |= T(acc ? 1u : 0u) << (8 * j);
+                resb[a * W] = acc ? rx + dx : rx;  // bin row offset after the attempt, for the measurement
+                rq = rx;
+                dq = dx;
+                pa = acc;
+                on = off1;
+                if (next) {
+                    thA = nA;
+                    thB = nB;
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < RPR; ++h) {
+                const int r = r0 + h, x0 = (c + r % L + (DIM == 3 ? r / L : 0)) & 1;
+                Rs[(r0 + h) * W + ln] ^= flipped[h] << (4 * x0);
+            }
+        }
+    }
+    __syncthreads();
+    // spins back to the multi-spin-coded global layout
+    constexpr uint32_t kOwned = W == 32 ? kFull : ((1u << W) - 1u);
+    for (int r2 = 0; r2 < NR; ++r2) {
+        const T Rw = Rs[r2 * W + ln];
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            const uint32_t m = __ballot_sync(kFull, ((Rw >> (4 * x)) & 1u) != 0) & kOwned;
+            if (lane == 0) spins[td.spin_off + r2 * L + x] = m;
+        }
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kCkThreads, 1)
+muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
+                    const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
+                    uint32_t *__restrict__ hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
+                    unsigned *__restrict__ diag) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileDesc td = tiles[blockIdx.x];
+    if (td.L & 1) return;  // odd L: the warp-per-chain colour kernel (whole CTA, before any barrier)
+    const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
+#define EAMC_CK(LL, WW) checker_tile<DIM, LL, WW>(td, blockIdx.x, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
+    if (td.width == 16) {
+        if constexpr (DIM == 3) {
+            if (td.L == 8) EAMC_CK(8, 16);
+        }
+        return;
+    }
+    switch (td.L) {
+        case 4: EAMC_CK(4, 32); break;
+        case 6: EAMC_CK(6, 32); break;
+        case 8: EAMC_CK(8, 32); break;
+        case 10: EAMC_CK(10, 32); break;
+        case 12: EAMC_CK(12, 32); break;
+        default: break;
+    }
+#undef EAMC_CK
+}
+
+template <int DIM, int W>
+size_t checker_smem_w(int L) {
+    switch (L) {
+        case 4: return CkGeo<DIM, 4, W>::SMEM;
+        case 6: return CkGeo<DIM, 6, W>::SMEM;
+        case 8: return CkGeo<DIM, 8, W>::SMEM;
+        case 10: return CkGeo<DIM, 10, W>::SMEM;
+        case 12: return CkGeo<DIM, 12, W>::SMEM;
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+size_t checker_smem_bytes(int dim, int L, int width) {
+    if ((L & 1) || L < 4 || L > 12) return 0;
+    if (width == 16) return (dim == 3 && L == 8) ? CkGeo<3, 8, 16>::SMEM : 0;
+    if (width != 32) return 0;
+    return dim == 3 ? checker_smem_w<3, 32>(L) : checker_smem_w<2, 32>(L);
+}
+
+cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,
+                                  uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr,
+                                  uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
+                                  unsigned *d_diag, cudaStream_t st) {
+    if (n_tiles <= 0 || n_sweeps == 0) return cudaSuccess;
+    static size_t set_limit[4] = {0, 0, 0, 0};
+    if (smem > set_limit[dim]) {
+        const cudaError_t e =
+            dim == 3 ? cudaFuncSetAttribute(muca_checker_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                     : cudaFuncSetAttribute(muca_checker_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_limit[dim] = smem;
+    }
+    if (dim == 3)
+        muca_checker_kernel<3><<<n_tiles, kCkThreads, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr, d_hist,
+                                                                 n_sweeps, key, count_rt, d_diag);
+    else
+        muca_checker_kernel<2><<<n_tiles, kCkThreads, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr, d_hist,
+                                                                 n_sweeps, key, count_rt, d_diag);
+    return cudaGetLastError();
+}
+
+}  // namespace eamc

@@ -436,12 +436,19 @@ __device__ __forceinline__ void sweep_tile(const TileDesc &td, int tile, SlotSta
             }
             const int offA = nA1 * NSB, offB = nB1 * NSB;
             const int aA0 = rq + offA, aB0 = rq + dxA + offB, aA1 = rB + offA, aB1 = rB + dxB + offB;
+            // the next attempt's loads go out before this attempt's threshold is used, so that
+            // their latency overlaps this decision (a warp issues in order)
+            uint32_t ldA = 0u, ldB = 0u;
+            if (next) {
+                ldA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + (pa ? aA1 : aA0)));
+                ldB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + (pa ? aB1 : aB0)));
+            }
             const uint32_t th = pa ? thB : thA;
             const int rx = pa ? rB : rq;
             const int dx = pa ? dxB : dxA;
             if (next) {
-                thA = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + (pa ? aA1 : aA0)));
-                thB = load_thr<G::SMEM_THR>(reinterpret_cast<const uint32_t *>(tab + (pa ? aB1 : aB0)));
+                thA = ldA;
+                thB = ldB;
             }
             if (x + 1 < L) {
                 nA = nA1;

@@ -18,6 +18,7 @@ EA_OK, EA_EINVAL, EA_ENOMEM, EA_ECUDA, EA_ETIMEOUT, EA_ESTATE = 0, -1, -2, -3, -
 EA_ALWAYS = 0xFFFFFFFF
 EA_FLAT, EA_POWERLAW, EA_ONE_OVER_K, EA_CANON = 0, 1, 2, 3
 EA_REC_PLAIN, EA_REC_BERG = 0, 1
+EA_ORDER_LEX, EA_ORDER_COLOUR = 0, 1
 
 
 class EamcError(RuntimeError):
@@ -117,6 +118,7 @@ SIGNATURES = {
     "ea_reset_chains": (_i, [P, P, _i, P, P]),
     "muca_set_sweep_multiplier": (_i, [P, _i, _i]),
     "muca_set_tile_width": (_i, [P, _i, _i]),
+    "muca_set_sweep_order": (_i, [P, _i, _i]),
     "muca_get_tile_width": (_i, [_i, _i, _i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i)]),
     "muca_update_weights_subset": (_i, [P, P, _i]),
     "muca_copy_weights": (_i, [P, P, P, _i]),
@@ -362,6 +364,10 @@ class Context:
         r = np.ascontiguousarray(rids, dtype=np.uint32)
         s = np.ascontiguousarray(streams, dtype=np.uint32)
         check(lib().ea_reset_chains(self._h, _p(c), c.shape[0], _p(r), _p(s)))
+
+    def set_sweep_order(self, order: int, chains_per_cta: int = 0):
+        """EA_ORDER_LEX or EA_ORDER_COLOUR for every chain of the context (see the header)."""
+        check(lib().muca_set_sweep_order(self._h, order, chains_per_cta))
 
     def set_tile_width(self, L: int, width: int):
         """Chains per tile (32, or 16 for L = 7, 8 in 3D) for chains of size L added
