@@ -32,7 +32,7 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-from paper_2011_08560_gb300.workloads import HEADLINE, L6_FLAT_PL, SMALL  # noqa: E402
+from paper_2011_08560_gb300.workloads import HEADLINE, L6_FLAT_PL, SMALL, order_code  # noqa: E402
 
 METRIC = "spin-flip attempts/ns (L=8, power-law ensemble)"
 UNIT = "attempts/ns"
@@ -42,10 +42,15 @@ UNIT = "attempts/ns"
 # 32 chains per word with extraction 3.5, threshold fetch and compare 3, flip and energy update
 # 2, lowest energy and round-trip check 1.5); the midpoint of the scope's 25-35
 ALG_OPS_PER_ATTEMPT = 30.0
-# per-chain latency floor of one MUCA attempt in SM cycles: with the next attempt's candidate
-# thresholds loaded one attempt ahead, two attempts cost one address select, one shared-memory
-# load (about 29 cycles, measured) and the compare / select of the decision, about 40 cycles
-LATENCY_FLOOR_CYCLES = 20.0
+# per-chain latency floor of one MUCA attempt in SM cycles: the next attempt's threshold is a
+# shared-memory load whose address depends on the current decision (the bin moves only if the
+# attempt is accepted), loaded for both outcomes one attempt ahead and selected.  That minimal
+# dependent pattern (select the address, load, select the threshold, compare), timed alone in one
+# warp with clock64 over 4096 steps on the GB300, takes 35.4 cycles per step (a chain of
+# dependent shared-memory loads: 34.0; compare -> select: 8.6; the same loads at independent
+# addresses pipeline at 9.2): the load's latency is not hidden once its address depends on the
+# decision it feeds, also with the loads issued two attempts ahead (32.4)
+LATENCY_FLOOR_CYCLES = 35.4
 # PT, per site word of 32 lattices (32 attempts): 12 word loads + 14 bit ops for the
 # unsatisfied counts + 4 for the classes, about 8 compared bit planes (2 Philox4x32-10 calls of
 # 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
@@ -69,12 +74,14 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
     ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
                                        "recursion", "scan", "small", "flat", "l6", "table_one_l8",
-                                       "paper_samples"],
+                                       "paper_samples", "lex"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner: narrow tiles where available, one launch per call "
                          "(a fixed launch sequence, for profiling)")
+    ap.add_argument("--order", choices=["lex", "colour"], default=None,
+                    help="sweep order of the headline chains (default: the workload's, colour)")
     ap.add_argument("--iter-steps", type=int, default=None,
                     help="weight-iteration steps before timing (default: the workload's)")
     ap.add_argument("--iter-sweeps", type=int, default=None,
@@ -95,8 +102,8 @@ def _oracle_worker(args):
     import numpy as np
 
     import oracle
-    dim, L, seed, rid, stream, kind, sweeps = args
-    c = oracle.Chain(dim, L, seed, rid, stream)
+    dim, L, seed, rid, stream, kind, sweeps, order = args
+    c = oracle.Chain(dim, L, seed, rid, stream, order=order)
     lnW = np.zeros(c.b_top + 1)
     for _ in range(2):
         c.sweeps(200, oracle.quantize(dim, lnW))
@@ -111,18 +118,19 @@ def _oracle_worker(args):
     return c.V * sweeps, dt, c.rt.n_rt
 
 
-def oracle_sample(target_s: float = 15.0, cores: int | None = None):
-    """Times the oracle on all host cores on a bounded sample of the headline workload."""
+def oracle_sample(target_s: float = 15.0, cores: int | None = None, W=HEADLINE):
+    """Times the oracle on all host cores on a bounded sample of the headline workload (in the
+    workload's sweep order)."""
     import oracle
     oracle.build()
     cores = cores or os.cpu_count() or 1
-    W = HEADLINE
+    order = order_code(W.order)
     # calibrate one chain
-    calib = _oracle_worker((W.dim, W.L, W.seed, 0, 0, 1, 50))
+    calib = _oracle_worker((W.dim, W.L, W.seed, 0, 0, 1, 50, order))
     per_sweep = calib[1] / 50
     chains = 2 * cores
     sweeps = max(20, int(target_s * cores / (chains * per_sweep)))
-    jobs = [(W.dim, W.L, W.seed, k, 0, 1, sweeps) for k in range(chains)]
+    jobs = [(W.dim, W.L, W.seed, k, 0, 1, sweeps, order) for k in range(chains)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         res = pool.map(_oracle_worker, jobs)
@@ -211,6 +219,8 @@ def headline(args):
         kw["iter_steps"] = args.iter_steps
     if args.iter_sweeps is not None:
         kw["iter_sweeps"] = args.iter_sweeps
+    if getattr(args, "order", None) is not None:
+        kw["order"] = args.order
     return dataclasses.replace(HEADLINE, **kw)
 
 
@@ -222,11 +232,12 @@ def build_context(eamc, rank: int, stream_ptr: int, W=HEADLINE, ensembles=None, 
     ens_list = ensembles or W.ensembles
     n = W.n_real
     if tuned:
-        best = autotune.tune([(W.dim, W.L, n)] * len(ens_list))
+        best = autotune.tune([(W.dim, W.L, n)] * len(ens_list), order=order_code(W.order))
     else:
         best = {"widths": {str(W.L): eamc.narrow_width(W.dim, W.L)}, "persistent": False,
                 "blocks_per_sm": 0, "sweeps_per_launch": 0}
     ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
+    ctx.set_sweep_order(order_code(W.order))
     if best:
         autotune.prepare(ctx, best)
     rid0 = shard_rid0(rank, n)
@@ -838,6 +849,37 @@ def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000):
             "table_one": res.table_one(pt_tau, pt_below), "paper_table_one": PAPER_TABLE_ONE[W.L]}
 
 
+def bench_order(order: str = "lex", n_real: int = 1024, S: int = 10_000, steps: int = 3,
+                iter_steps: int = 4, iter_sweeps: int = 2000):
+    """The headline workload with the sites of a sweep in another order (the paper fixes none):
+    same chains, same weight recursion (short iteration: the throughput of a production sweep
+    does not depend on how far the weights converged), autotuned tile width and launch."""
+    import dataclasses
+
+    import torch
+
+    from paper_2011_08560_gb300 import eamc
+    W = dataclasses.replace(HEADLINE, n_real=n_real, iter_steps=iter_steps, iter_sweeps=iter_sweeps,
+                            order=order)
+    stream = torch.cuda.Stream()
+    ctx = build_context(eamc, 0, stream.cuda_stream, W)
+    iterate_weights(ctx, W, stream)
+    ctx.run_sweeps(S // 10, count_roundtrips=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.run_sweeps(S, count_roundtrips=True)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    launch = getattr(ctx, "tuned", None)
+    ctx.check()
+    ctx.close()
+    return {"workload": f"3D L={W.L}, {n_real} realizations, power law (-3.6, 96), sweep order {order}, "
+                        f"{steps} x {S} production sweeps after {iter_steps} x {iter_sweeps} Berg iteration sweeps",
+            "attempts_per_ns": n_real * W.L ** 3 * S * steps / (ms * 1e6), "launch": launch}
+
+
 def bench_paper_samples(n_real: int = 4096, S: int = 10_000, steps: int = 3, iter_steps: int = 4,
                         iter_sweeps: int = 2000):
     """The headline ensemble (L=8, power law, production with frozen weights) at the paper's
@@ -954,6 +996,8 @@ def main():
               "weight_iteration": f"{W.iter_steps} x {W.iter_sweeps} sweeps, {W.recursion} recursion, "
                                   f"before timing; then E_g fixed, weights frozen",
               "step": "production sweeps with histogram, lowest-energy and round-trip measurement",
+              "sweep_order": {"lex": "lexicographic", "colour": "checkerboard (colour class by colour "
+                              "class, each in lexicographic order)"}[W.order],
               "l2": "flushed between steps (256 MB write)",
               "parallelism": f"independent realizations, {world} GPU(s)"}
 
@@ -964,7 +1008,7 @@ def main():
         per = max(4.0, 60.0 / max(1, args.steps + args.warmup))
         base = None
         for k in range(args.warmup + args.steps):
-            base = oracle_sample(target_s=min(per, 20.0))
+            base = oracle_sample(target_s=min(per, 20.0), W=W)
             if k >= args.warmup:
                 steps.append(base)
         val = statistics.mean(s["value"] for s in steps)
@@ -985,7 +1029,7 @@ def main():
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "recursion": bench_recursion, "small": bench_small, "flat": bench_flat_same_schedule,
               "serving_saturated": bench_serving_saturated, "table_one_l8": bench_table_one_l8,
-              "paper_samples": bench_paper_samples,
+              "paper_samples": bench_paper_samples, "lex": lambda: bench_order("lex"),
               "l6": bench_l6_flat_pl}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
         return
@@ -994,11 +1038,12 @@ def main():
         torch.distributed.init_process_group("nccl")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample()      # spawn pool before the first CUDA call
+        cpu = oracle_sample(W=W)   # spawn pool before the first CUDA call
     r = run_gpu(args, rank, world)
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = {"paper_samples_l8": bench_paper_samples(), "table_one_l8": bench_table_one_l8(),
+        extras = {"headline_lexicographic": bench_order("lex"),
+                  "paper_samples_l8": bench_paper_samples(), "table_one_l8": bench_table_one_l8(),
                   "l6_flat_pl": bench_l6_flat_pl(),
                   "small": bench_small(), "pt": bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol(),
                   "uneven": bench_uneven(), "serving": bench_serving(),
@@ -1040,7 +1085,7 @@ def main():
                      "frac": r["achieved_ops"] / r["alu_peak"], "traffic": SWEEP_TRAFFIC_BYTES,
                      "traffic_basis": "ncu dram read+write of one launch (one-time table and lattice "
                                       "staging, independent of the sweeps per launch)",
-                     "kernel": "muca_sweep_kernel<3>",
+                     "kernel": "muca_checker_kernel<3>" if W.order == "colour" else "muca_sweep_kernel<3>",
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock "
                                    f"(MEASURED_PEAKS.json sm_max_mhz)"},

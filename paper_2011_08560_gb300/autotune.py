@@ -9,6 +9,9 @@ Knobs:
     persistent grid (chains are latency-bound, so tiles sharing an SM sub-partition slow each
     other down);
   * sweeps per launch.
+In the colour order (muca_set_sweep_order) the even-L chains run in their own kernel, one block
+per tile: there only the tile width is tuned.  The order itself is the caller's choice (it changes
+the trajectories), never the tuner's.
 A candidate is timed with CUDA events on a scratch context with the same composition of chains
 (same dim, L and chain counts, a different seed), so tuning never advances the caller's chains,
 whose results do not depend on the choice anyway.  The winner is cached in a JSON file keyed by
@@ -65,11 +68,13 @@ def _store(db):
     os.replace(tmp, CACHE)
 
 
-def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, device: int = 0):
-    """Returns the fastest configuration for this composition of chains:
+def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, device: int = 0,
+         order: int = 0):
+    """Returns the fastest configuration for this composition of chains in sweep order `order`:
     {"widths": {L: width}, "persistent", "blocks_per_sm", "sweeps_per_launch"}."""
     import torch
-    key = f"{torch.cuda.get_device_name(device)}|{signature(groups)}|{sweeps}"
+    key = f"{torch.cuda.get_device_name(device)}|{signature(groups)}|{sweeps}|order{order}"
+    launches = LAUNCHES if order == 0 else LAUNCHES[:1]
     db = _load() if use_cache else {}
     if key in db:
         return db[key]["best"]
@@ -77,13 +82,14 @@ def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, dev
     results = []
     for widths in width_options(groups):
         ctx = eamc.Context(seed=0x5EED, device=device, stream=stream.cuda_stream)
+        ctx.set_sweep_order(order)
         for L, w in widths.items():
             ctx.set_tile_width(int(L), w)
         rid = 0
         for dim, L, n in groups:
             ctx.init_disorder(dim, L, n, rid0=rid)
             rid += n
-        for cand in LAUNCHES:
+        for cand in launches:
             ctx.set_launch(cand["persistent"], cand["sweeps_per_launch"], cand["blocks_per_sm"])
             ctx.run_sweeps(max(2, sweeps // 8))  # warm-up
             best = None

@@ -26,6 +26,9 @@ class MucaWorkload:
     iter_sweeps: int = 0
     recursion: str = "berg"
     prod_sweeps: int = 0
+    # order of the attempts within a sweep: "lex" (lexicographic) or "colour" (colour class by
+    # colour class, the checkerboard for even L); the paper fixes none
+    order: str = "lex"
 
 
 # L=4, one realization, flat MUCA: 20 x 10^4 iteration sweeps, then 10^5 production sweeps;
@@ -35,11 +38,12 @@ SMALL = MucaWorkload("3D +-J EA L=4, 1 realization (seed 1), flat MUCA, 20 x 10^
                      recursion="plain", prod_sweeps=100_000)
 
 # the headline: L=8, 1024 realizations, power-law MUCA (alpha = -3.6, Delta E = 96); weights
-# from Berg's recursion, then E_g fixed and round trips counted in production sweeps
+# from Berg's recursion, then E_g fixed and round trips counted in production sweeps; sites in
+# the checkerboard order
 HEADLINE = MucaWorkload("3D +-J EA L=8, 1024 realizations, power-law MUCA (alpha=-3.6, "
-                        "Delta E=96), production with frozen weights", 3, 8, 1024, seed=2,
-                        ensembles=("powerlaw",), sweeps=10_000, iter_steps=60,
-                        iter_sweeps=10_000, recursion="berg")
+                        "Delta E=96), production with frozen weights, checkerboard sweeps", 3, 8,
+                        1024, seed=2, ensembles=("powerlaw",), sweeps=10_000, iter_steps=60,
+                        iter_sweeps=10_000, recursion="berg", order="colour")
 
 # L=6, 1024 realizations, flat MUCA beside the power-law ensemble (2048 chains)
 L6_FLAT_PL = MucaWorkload("3D +-J EA L=6, 1024 realizations, flat MUCA + power-law MUCA", 3, 6,
@@ -53,6 +57,11 @@ UNEVEN = dict(dim=3, Ls=(4, 6, 8, 10, 12), n_real=4096, seed=4)
 
 # serving: Poisson arrivals, L in {4..12}, round-trip targets log-uniform in [10, 1000]
 SERVING = dict(rate_hz=200.0, Ls=(4, 5, 6, 7, 8, 9, 10, 11, 12), rt_min=10, rt_max=1000, seed=5)
+
+
+def order_code(order: str) -> int:
+    """The library's sweep-order constant (EA_ORDER_LEX 0, EA_ORDER_COLOUR 1) of a workload."""
+    return {"lex": 0, "colour": 1}[order]
 
 
 def geometric_betas(M: int, beta_min: float, beta_max: float):

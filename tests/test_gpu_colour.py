@@ -1,7 +1,8 @@
-"""The colour-order sweep kernel (sites colour class by colour class, attempts resolved eight at
-a time from acceptance masks over the reachable bins) against the oracle's colour order,
-element by element: spins, energies, histograms and round-trip records bit-exact, weights to
-1e-12; for every block size (chains per CTA), launch splitting, captured graphs and the weight
+"""The colour-order sweep kernels against the oracle's colour order, element by element: spins,
+energies, histograms and round-trip records bit-exact, weights to 1e-12.  Even L runs the
+checkerboard kernel (one lane per chain; records of two or four rows, one or two records of
+look-ahead, 2D and 3D, full and narrow tiles), odd L the warp-per-chain kernel (every block
+size); launch splitting, captured graphs, contexts holding both parities and the weight
 recursions."""
 import numpy as np
 import pytest
@@ -60,7 +61,8 @@ def _compare(ctx, chains, chain0=0, hist=True, rt=True):
 @pytest.mark.parametrize("dim,L,n,sweeps,cpc", [
     (3, 4, 40, 120, 0), (3, 3, 33, 100, 4), (3, 5, 7, 40, 2), (3, 6, 64, 40, 8), (2, 4, 35, 300, 8),
     (2, 5, 9, 200, 1), (3, 7, 19, 40, 0), (3, 8, 32, 30, 4), (3, 9, 5, 12, 0), (3, 10, 33, 8, 2),
-    (3, 11, 3, 6, 1), (3, 12, 3, 5, 0), (3, 4, 1, 200, 0)])
+    (3, 11, 3, 6, 1), (3, 12, 3, 5, 0), (3, 4, 1, 200, 0),
+    (2, 6, 33, 200, 0), (2, 8, 5, 150, 0), (2, 10, 9, 100, 0), (2, 12, 40, 60, 0)])
 def test_colour_sweeps_bit_exact(eamc, orc, dim, L, n, sweeps, cpc):
     rng = np.random.default_rng(L * 100 + n)
     ctx = eamc.Context(seed=SEED)

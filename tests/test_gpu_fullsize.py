@@ -41,17 +41,19 @@ def _check(ctx, orc, c, ch, lnW):
     _rt_equal(ctx.roundtrips(c, 1)[0], ch.rt)
 
 
-def test_headline_full_size_sampled(eamc, orc):
+@pytest.mark.parametrize("order", ["colour", "lex"])
+def test_headline_full_size_sampled(eamc, orc, order):
     """The headline as bench.py builds and launches it: 1024 power-law chains of L=8 with Berg's
     recursion, a (shortened) iteration phase, E_g fixed and records reset, then one production
-    step of 10^4 sweeps with round-trip counting; sampled chains replayed by the oracle."""
+    step of 10^4 sweeps with round-trip counting; sampled chains replayed by the oracle.  In the
+    headline's sweep order (the checkerboard) and in the lexicographic order."""
     import dataclasses
 
     import torch
 
     import bench
-    from paper_2011_08560_gb300.workloads import HEADLINE
-    W = dataclasses.replace(HEADLINE, iter_steps=4, iter_sweeps=1000)
+    from paper_2011_08560_gb300.workloads import HEADLINE, order_code
+    W = dataclasses.replace(HEADLINE, iter_steps=4, iter_sweeps=1000, order=order)
     stream = torch.cuda.Stream()
     ctx = bench.build_context(eamc, 0, stream.cuda_stream, W)
     assert ctx.num_chains() == W.n_real == 1024
@@ -61,7 +63,7 @@ def test_headline_full_size_sampled(eamc, orc):
     ctx.synchronize()
     H = ctx.histograms()
     for rid in (0, 511, 1023):
-        ch = orc.Chain(W.dim, W.L, W.seed, rid, 0)
+        ch = orc.Chain(W.dim, W.L, W.seed, rid, 0, order=order_code(W.order))
         lnW = np.zeros(ch.b_top + 1)
         acc = orc.berg_state(ch.b_top + 1)
         for _ in range(W.iter_steps):
