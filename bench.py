@@ -507,15 +507,16 @@ def _small_oracle_full():
             "t_first": c.rt.t_first, "t_last": c.rt.t_last, "E": c.E, "e_g": c.rt.e_g}
 
 
-def bench_small():
-    """Config 1: L=4, one realization, flat MUCA, 20 x 10^4 iteration sweeps then 10^5
-    production sweeps, on the GPU and (in full, one core) in the oracle; same trajectory."""
+def _small_gpu(order: int):
+    """Config 1 on the GPU in sweep order `order`: device ms of the iteration and production
+    phases, the round-trip record and the final energy."""
     import torch
 
     from paper_2011_08560_gb300 import eamc
     W = SMALL
     stream = torch.cuda.Stream()
     ctx = eamc.Context(seed=W.seed, device=0, stream=stream.cuda_stream)
+    ctx.set_sweep_order(order)
     ctx.init_disorder(W.dim, W.L, 1, rid0=0, stream=0)
     ctx.set_ensemble(0, 1, eamc.EA_FLAT)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -535,8 +536,18 @@ def bench_small():
     rec = ctx.roundtrips()[0]
     _, E, _ = ctx.state(spins=False)
     ctx.close()
+    return it_ms, prod_ms, rec, int(E[0])
+
+
+def bench_small():
+    """Config 1: L=4, one realization, flat MUCA, 20 x 10^4 iteration sweeps then 10^5
+    production sweeps, on the GPU and (in full, one core) in the oracle; same trajectory.  Also
+    timed on the GPU in the checkerboard order (a different trajectory of the same ensemble)."""
+    W = SMALL
+    it_ms, prod_ms, rec, E = _small_gpu(0)
+    it_c, prod_c, rec_c, _ = _small_gpu(1)
     orc = _small_oracle_full()
-    same = (rec["n_rt"], rec["t_first"], rec["t_last"], int(E[0]), rec["e_g"]) == \
+    same = (rec["n_rt"], rec["t_first"], rec["t_last"], E, rec["e_g"]) == \
         (orc["n_rt"], orc["t_first"], orc["t_last"], orc["E"], orc["e_g"])
     V = W.L ** W.dim
     total = V * (W.iter_steps * W.iter_sweeps + W.prod_sweeps)
@@ -546,7 +557,10 @@ def bench_small():
             "round_trips": rec["n_rt"], "tau_sweeps": (rec["t_last"] - rec["t_first"]) / rec["n_rt"] if rec["n_rt"] else None,
             "oracle_seconds_one_core": orc["seconds"], "oracle_attempts_per_ns": total / (orc["seconds"] * 1e9),
             "oracle_production_round_trips_per_s": orc["n_rt"] / orc["production_seconds"],
-            "same_trajectory_as_oracle": same}
+            "same_trajectory_as_oracle": same,
+            "checkerboard": {"gpu_ms": it_c + prod_c, "gpu_attempts_per_ns": total / ((it_c + prod_c) * 1e6),
+                             "round_trips": rec_c["n_rt"],
+                             "gpu_production_round_trips_per_s": rec_c["n_rt"] / (prod_c / 1e3)}}
 
 
 def bench_pt(S: int = 100_000, equil: int = 10_000, sample_every: int = 100):
