@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
     ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
                                        "recursion", "scan", "small", "flat", "l6", "table_one_l8",
-                                       "paper_samples", "lex"],
+                                       "paper_samples", "lex", "uneven_checkerboard"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--no-tune", action="store_true",
@@ -680,13 +680,14 @@ def uneven_groups():
     return out
 
 
-def build_uneven(eamc, autotune, stream_ptr, S: int):
+def build_uneven(eamc, autotune, stream_ptr, S: int, order: int = 0):
     """The uneven batch as the bench runs it: chains, autotuned launch, one iteration step, then
     the 1/k chains take 1/k weights built from their estimate."""
     from paper_2011_08560_gb300.workloads import UNEVEN
     groups = [(3, L, n) for _, L, _, n in uneven_groups()]
-    best = autotune.tune(groups, sweeps=20)
+    best = autotune.tune(groups, sweeps=20, order=order)
     ctx = eamc.Context(seed=UNEVEN["seed"], device=0, stream=stream_ptr)
+    ctx.set_sweep_order(order)
     autotune.prepare(ctx, best)
     one_over_k = []
     for kind_idx, L, rid0, n in uneven_groups():
@@ -702,15 +703,16 @@ def build_uneven(eamc, autotune, stream_ptr, S: int):
     return ctx, groups, best
 
 
-def bench_uneven(S: int = 100, iters: int = 3):
+def bench_uneven(S: int = 100, iters: int = 3, order: int = 0):
     """Uneven batch: 4096 realizations, L uniform over {4,6,8,10,12} (round robin by id), each
-    as a power-law, a flat and a 1/k chain, in one persistent launch per step; the
+    as a power-law, a flat and a 1/k chain, in one launch per step (lexicographic order: the
+    persistent work-queue kernel; checkerboard order: one block per tile); the
     weight-iteration loop is a captured CUDA graph."""
     import torch
 
     from paper_2011_08560_gb300 import autotune, eamc
     stream = torch.cuda.Stream()
-    ctx, groups, best = build_uneven(eamc, autotune, stream.cuda_stream, S)
+    ctx, groups, best = build_uneven(eamc, autotune, stream.cuda_stream, S, order)
     attempts_per_sweep = sum(n * L ** 3 for _, L, n in groups)
     ctx.graph_capture(n_iter=iters, sweeps_per_iter=S, count_roundtrips=True, update_weights=True)
     ctx.graph_launch(1)
@@ -723,7 +725,8 @@ def bench_uneven(S: int = 100, iters: int = 3):
     ms = e0.elapsed_time(e1)
     ctx.close()
     return {"workload": "4096 realizations, L in {4,6,8,10,12} round robin, x3 ensembles "
-                        "(power law, flat, 1/k), graph-captured iteration loop",
+                        "(power law, flat, 1/k), graph-captured iteration loop, sweep order "
+                        + ("checkerboard" if order else "lexicographic"),
             "chains": sum(n for _, _, n in groups), "graph": f"{iters} x ({S} sweeps + weight update)",
             "ms": ms, "attempts_per_ns": attempts_per_sweep * S * iters / (ms * 1e6), "launch": best}
 
@@ -1040,7 +1043,8 @@ def main():
 
     if args.only:
         fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
-              "uneven": bench_uneven, "serving": bench_serving,
+              "uneven": bench_uneven, "uneven_checkerboard": lambda: bench_uneven(order=1),
+              "serving": bench_serving,
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "recursion": bench_recursion, "small": bench_small, "flat": bench_flat_same_schedule,
               "serving_saturated": bench_serving_saturated, "table_one_l8": bench_table_one_l8,
