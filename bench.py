@@ -142,6 +142,7 @@ def oracle_sample(target_s: float = 15.0, cores: int | None = None, W=HEADLINE):
     return {"value": attempts / (wall * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{chains} power-law chains of L={W.L} (realizations 0..{chains - 1}), "
                       f"{sweeps} production sweeps each with frozen weights and round-trip counting, "
+                      f"sites in the {'colour (checkerboard)' if order else 'lexicographic'} order, "
                       f"{busy:.1f} s of CPU time on {cores} processes",
             "round_trips": sum(r[2] for r in res), "wall_s": wall}
 

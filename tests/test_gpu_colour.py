@@ -157,3 +157,48 @@ def test_sweep_order_rejects_bad_arguments(eamc):
     for order, cpc in ((2, 0), (1, 3), (1, 16), (-1, 0)):
         with pytest.raises(eamc.EamcError):
             ctx.set_sweep_order(order, cpc)
+
+
+def test_colour_snapshot_resume_and_narrow_tiles(eamc, orc):
+    """The colour order continues a snapshot bit-exactly (the order is the caller's setting, not
+    part of the snapshot): 2 x 30 sweeps straight == 30, snapshot, restore, 30; chains of an even
+    (checkerboard kernel, 16-chain tiles) and an odd size (warp-per-chain kernel) in one context;
+    the oracle's colour order agrees."""
+    def make():
+        ctx = eamc.Context(seed=SEED)
+        ctx.set_sweep_order(eamc.EA_ORDER_COLOUR)
+        ctx.set_tile_width(8, 16)
+        ctx.init_disorder(3, 8, 18, rid0=3)
+        ctx.init_disorder(3, 7, 5, rid0=30, stream=1)
+        ctx.set_ensemble(0, 23, eamc.EA_POWERLAW, -3.6, 96.0)
+        return ctx
+
+    def run(ctx, steps):
+        for _ in range(steps):
+            ctx.run_sweeps(30, count_roundtrips=True)
+            ctx.update_weights()
+
+    straight = make()
+    run(straight, 2)
+    first = make()
+    run(first, 1)
+    blob = first.snapshot()
+    resumed = eamc.Context(seed=999)
+    resumed.restore(blob)
+    resumed.set_sweep_order(eamc.EA_ORDER_COLOUR)
+    run(resumed, 1)
+    S1, E1, t1 = straight.state()
+    S2, E2, t2 = resumed.state()
+    assert np.array_equal(S1, S2) and np.array_equal(E1, E2) and np.array_equal(t1, t2)
+    assert np.array_equal(straight.get_weights(), resumed.get_weights())
+    chains = _chains(orc, 3, 8, 18, 3) + _chains(orc, 3, 7, 5, 30, 1)
+    lnW = [np.zeros(c.b_top + 1) for c in chains]
+    for _ in range(2):
+        for k, c in enumerate(chains):
+            c.sweeps(30, orc.quantize(3, lnW[k]), count_rt=True)
+            lnW[k] = orc.update_weights(3, c.L, c.parity, orc.POWERLAW, -3.6, 96.0, c.rt.e_min, lnW[k], c.hist)
+            c.hist[:] = 0
+            c.rt.e_g = c.rt.e_min
+    for k, c in enumerate(chains):
+        assert np.array_equal(S2[k, :c.V], c.S) and E2[k] == c.E
+    resumed.check()
