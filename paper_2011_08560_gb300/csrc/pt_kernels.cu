@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, 1) pt_kernel(PtArgs a) {
                 }
                 (void)c2;
                 (void)c3;
-                // the lanes of this warp that have an item in this round (items are consecutive)
+                // the lanes of this warp that have an item in this pass of the loop (items are consecutive)
                 const int rem = spc * nc - (item - lane);
                 const uint32_t live = rem >= 32 ? kFull : ((1u << rem) - 1u);
                 const bool open = und != 0u;
