@@ -363,7 +363,8 @@ int pt_adapt(ea_ctx *ctx, double eta);
  * the switch to production, requeue, completion).  The host never waits for a tick: finished
  * jobs are read back asynchronously every poll_ticks ticks.  A job's schedule is counted in its
  * own ticks and its random numbers are keyed by its own sweep counter, so its result is the same
- * alone and among other jobs.  A server is not thread-safe. */
+ * alone and among other jobs.  Served chains sweep in the lexicographic order.  A server is not
+ * thread-safe. */
 typedef struct ea_srv ea_srv;
 
 typedef struct {
@@ -455,7 +456,7 @@ int ea_srv_context(ea_srv *srv, ea_ctx **ctx);
  * The paper has no counterpart to this entry point: it serves callers that cannot allocate
  * device memory (code inside another framework's memory pool or under a fixed device-memory
  * budget, plugins that may only touch the buffers they are given).  It runs n_sweeps MUCA
- * sweeps (the muca_run_sweeps kernel, without round-trip counting) on n chains of linear size
+ * sweeps (the muca_run_sweeps kernel in the lexicographic order, without round-trip counting) on n chains of linear size
  * L without a context and without allocating anything: no cudaMalloc, no cudaFree, no
  * allocating library call.  Its working memory is one static device array of 4 MiB in the
  * library, which every GPU that loads the library holds until the process exits; at most
