@@ -62,7 +62,8 @@ def _compare(ctx, chains, chain0=0, hist=True, rt=True):
     (3, 4, 40, 120, 0), (3, 3, 33, 100, 4), (3, 5, 7, 40, 2), (3, 6, 64, 40, 8), (2, 4, 35, 300, 8),
     (2, 5, 9, 200, 1), (3, 7, 19, 40, 0), (3, 8, 32, 30, 4), (3, 9, 5, 12, 0), (3, 10, 33, 8, 2),
     (3, 11, 3, 6, 1), (3, 12, 3, 5, 0), (3, 4, 1, 200, 0),
-    (2, 6, 33, 200, 0), (2, 8, 5, 150, 0), (2, 10, 9, 100, 0), (2, 12, 40, 60, 0)])
+    (2, 6, 33, 200, 0), (2, 8, 5, 150, 0), (2, 10, 9, 100, 0), (2, 12, 40, 60, 0),
+    (3, 10, 40, 24, 0), (3, 12, 33, 16, 0)])
 def test_colour_sweeps_bit_exact(eamc, orc, dim, L, n, sweeps, cpc):
     rng = np.random.default_rng(L * 100 + n)
     ctx = eamc.Context(seed=SEED)
