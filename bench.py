@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the PT / uneven / serving lines")
     ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
                                        "recursion", "scan", "small", "flat", "l6", "table_one_l8",
-                                       "paper_samples", "lex", "uneven_checkerboard"],
+                                       "paper_samples", "lex", "uneven_checkerboard",
+                                       "table_one_l8_checkerboard", "scan_checkerboard"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--no-tune", action="store_true",
@@ -792,14 +793,14 @@ PAPER_TABLE_ONE = {3: {"flat": (1.160, 1.174), "1/k": (1.0146, 1.0193), "PT": (1
 
 
 def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_sweeps: int = 10000,
-                       prod_sweeps: int = 100000, pt: bool = True):
+                       prod_sweeps: int = 100000, pt: bool = True, order: int = 0):
     """Profile-parameter scan (Sec. II): power-law alpha x Delta E grid, flat and 1/k beside
     it, n_real realizations of L^3, density of states once per realization (power-law target,
     Berg's recursion), production with round-trip counting in one batched launch; PT with the
     paper's replica count on the same realizations.  Reports the mean round-trip time per
     ensemble, its ratio to flat, and the Table I analog: r_pop and r_eps (eps = 1e-4) of flat,
     1/k and PT relative to the power law (-3.6, 96), with jackknife errors, beside the paper's
-    values (other disorder sets: context, not a target)."""
+    values (other disorder sets: context, not a target).  The MUCA chains sweep in `order`."""
     import time
 
     import numpy as np
@@ -811,7 +812,7 @@ def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_
     t0 = time.perf_counter()
     res = scan.profile_scan(3, L, n_real, alphas, poles, seed=6, dos_iters=dos_iters,
                             dos_sweeps=dos_sweeps, prod_sweeps=prod_sweeps,
-                            recursion=eamc.EA_REC_BERG, stream=stream.cuda_stream)
+                            recursion=eamc.EA_REC_BERG, stream=stream.cuda_stream, order=order)
     wall = time.perf_counter() - t0
     pt_tau = pt_below = None
     M = PT_REPLICAS.get(L)
@@ -823,7 +824,8 @@ def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_
     out = {"workload": f"3D L={L}, {n_real} realizations (seed 6), power law alpha in {list(alphas)} x "
                        f"Delta E in {list(poles)}, flat and 1/k; density of states {dos_iters} x "
                        f"{dos_sweeps} sweeps (Berg), {prod_sweeps} production sweeps; PT with M = {M} "
-                       f"replicas, beta in [0.3, 2.15] adapted over 8 x 1000 sweeps, {prod_sweeps} sweeps",
+                       f"replicas, beta in [0.3, 2.15] adapted over 8 x 1000 sweeps, {prod_sweeps} sweeps; "
+                       f"MUCA sites in the {'checkerboard' if order else 'lexicographic'} order",
            "wall_s": wall, "pt_wall_s": wall_pt, "best_power_law": res.best(),
            "ensembles": {r["ensemble"]: {k: v for k, v in r.items() if k != "ensemble"} for r in rows},
            "table_one": res.table_one(pt_tau, pt_below),
@@ -835,11 +837,12 @@ def bench_profile_scan(L: int = 6, n_real: int = 128, dos_iters: int = 100, dos_
     return out
 
 
-def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000):
+def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000, order: int = 0):
     """Table I analog at the headline's size, L=8, on its 1024 realizations: one density of
     states per realization from the headline's power-law Berg iteration, shared by flat MUCA,
     the power law (-3.6, 96) and the 1/k ensemble (each a chain of its own), and PT with the
-    paper's M = 20 on the same realizations; production with round-trip counting."""
+    paper's M = 20 on the same realizations; production with round-trip counting.  The MUCA
+    chains sweep in `order` (0 lexicographic, 1 checkerboard)."""
     import time
 
     import numpy as np
@@ -851,7 +854,8 @@ def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000):
     t0 = time.perf_counter()
     res = scan.profile_scan(3, W.L, n_real, (W.alpha,), (W.pole,), seed=W.seed, dos_iters=W.iter_steps,
                             dos_sweeps=W.iter_sweeps, prod_sweeps=prod_sweeps, recursion=eamc.EA_REC_BERG,
-                            stream=stream.cuda_stream, tile_width=eamc.narrow_width(3, W.L))
+                            stream=stream.cuda_stream, tile_width=eamc.narrow_width(3, W.L),
+                            order=order)
     wall = time.perf_counter() - t0
     pt_tau, pt_below = scan.pt_round_trips(3, W.L, n_real, PT_REPLICAS[W.L], res.e_g, seed=W.seed,
                                            prod_sweeps=prod_sweeps, stream=stream.cuda_stream)
@@ -863,7 +867,8 @@ def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000):
     return {"workload": f"3D L={W.L}, {n_real} realizations (seed {W.seed}), density of states from "
                         f"{W.iter_steps} x {W.iter_sweeps} power-law Berg sweeps, flat / power law "
                         f"(-3.6, 96) / 1/k chains from it, PT with M = {PT_REPLICAS[W.L]}; {prod_sweeps} "
-                        f"production sweeps each",
+                        f"production sweeps each; MUCA sites in the "
+                        f"{'checkerboard' if order else 'lexicographic'} order",
             "wall_s": time.perf_counter() - t0, "muca_wall_s": wall, "ensembles": rows,
             "table_one": res.table_one(pt_tau, pt_below), "paper_table_one": PAPER_TABLE_ONE[W.L]}
 
@@ -1047,8 +1052,11 @@ def main():
               "uneven": bench_uneven, "uneven_checkerboard": lambda: bench_uneven(order=1),
               "serving": bench_serving,
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
+              "scan_checkerboard": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps,
+                                                              order=1),
               "recursion": bench_recursion, "small": bench_small, "flat": bench_flat_same_schedule,
               "serving_saturated": bench_serving_saturated, "table_one_l8": bench_table_one_l8,
+              "table_one_l8_checkerboard": lambda: bench_table_one_l8(order=1),
               "paper_samples": bench_paper_samples, "lex": lambda: bench_order("lex"),
               "l6": bench_l6_flat_pl}
         print(json.dumps({"only": args.only, **fn[args.only]()}))
@@ -1064,11 +1072,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {"headline_lexicographic": bench_order("lex"),
                   "paper_samples_l8": bench_paper_samples(), "table_one_l8": bench_table_one_l8(),
+                  "table_one_l8_checkerboard": bench_table_one_l8(order=1),
                   "l6_flat_pl": bench_l6_flat_pl(),
                   "small": bench_small(), "pt": bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol(),
                   "uneven": bench_uneven(), "serving": bench_serving(),
                   "serving_saturated": bench_serving_saturated(), "recursion": bench_recursion(),
-                  "scan": bench_profile_scan()}
+                  "scan": bench_profile_scan(), "scan_checkerboard": bench_profile_scan(order=1)}
     if rank != 0:
         if world > 1:
             import torch

@@ -125,11 +125,14 @@ def pt_round_trips(dim: int, L: int, n_real: int, M: int, e_g, seed: int = 0, ri
 def profile_scan(dim: int, L: int, n_real: int, alphas, poles, seed: int = 0, rid0: int = 0,
                  dos_iters: int = 30, dos_sweeps: int = 2000, recursion: int = eamc.EA_REC_BERG,
                  dos_alpha: float = -3.6, dos_pole: float = 96.0, prod_sweeps: int = 20000,
-                 with_one_over_k: bool = True, stream=None, tile_width: int = 32) -> ScanResult:
+                 with_one_over_k: bool = True, stream=None, tile_width: int = 32,
+                 order: int = 0) -> ScanResult:
     """Runs the three stages above for every (alpha, Delta E) in alphas x poles (tile_width:
-    chains per tile, see muca_set_tile_width)."""
+    chains per tile, see muca_set_tile_width; order: the sites' order within a sweep,
+    muca_set_sweep_order, for every stage)."""
     ctx = eamc.Context(seed=seed, stream=stream)
     try:
+        ctx.set_sweep_order(order)
         if tile_width != 32:
             ctx.set_tile_width(L, tile_width)
         # 1. density of states (power-law target, stream 0)

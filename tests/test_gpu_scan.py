@@ -39,15 +39,17 @@ def test_copy_weights(eamc):
         ctx.copy_weights([0, 4], [4, 5])    # 4 is source and destination
 
 
-def test_profile_scan_matches_oracle(eamc, orc):
+@pytest.mark.parametrize("order", [0, 1])
+def test_profile_scan_matches_oracle(eamc, orc, order):
+    """In both sweep orders (order 1: the checkerboard kernel at L = 4)."""
     from paper_2011_08560_gb300 import scan
     dim, L, n, seed = 3, 4, 5, 13
     iters, S, P = 6, 400, 2500
     res = scan.profile_scan(dim, L, n, (-3.6, -2.0), (96.0, 30.0), seed=seed, dos_iters=iters,
-                            dos_sweeps=S, prod_sweeps=P, recursion=eamc.EA_REC_BERG)
+                            dos_sweeps=S, prod_sweeps=P, recursion=eamc.EA_REC_BERG, order=order)
     assert res.labels[0] == "flat" and res.labels[-1] == "1/k" and len(res.labels) == 6
     for r in range(n):
-        dos = orc.Chain(dim, L, seed, r, 0)
+        dos = orc.Chain(dim, L, seed, r, 0, order=order)
         lnW = np.zeros(dos.b_top + 1)
         acc = orc.berg_state(dos.b_top + 1)
         for _ in range(iters):
@@ -61,7 +63,7 @@ def test_profile_scan_matches_oracle(eamc, orc):
                         for b in range(dos.b_top + 1)])
         lnO = lnP - lnW
         for k, (kind, a, p) in enumerate(res.params):
-            ch = orc.Chain(dim, L, seed, r, stream=1 + k)
+            ch = orc.Chain(dim, L, seed, r, stream=1 + k, order=order)
             if kind != 1:
                 a, p = -3.6, 96.0
             w = orc.build_weights(dim, L, ch.parity, kind, a, p, 1.0, e_g, lnO)
