@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
                                        "recursion", "scan", "small", "flat", "l6", "table_one_l8",
                                        "paper_samples", "lex", "uneven_checkerboard",
-                                       "table_one_l8_checkerboard", "scan_checkerboard"],
+                                       "table_one_l8_checkerboard", "scan_checkerboard", "serving_colour"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--no-tune", action="store_true",
@@ -934,24 +934,25 @@ def bench_paper_samples(n_real: int = 4096, S: int = 10_000, steps: int = 3, ite
             "attempts_per_ns": n_real * W.L ** 3 * S * steps / (ms * 1e6), "launch": launch}
 
 
-def bench_serving(window_s: float = 10.0, drain_s: float = 30.0):
+def bench_serving(window_s: float = 10.0, drain_s: float = 30.0, order: int = 0):
     """Serving (config 5): Poisson arrivals (200 jobs/s) of realization jobs, L in {4..12},
     round-trip targets log-uniform in [10, 1000]; power-law MUCA with Berg's recursion; state
     resident on the device, admission by memory, job control on the device, asynchronous
-    read-back.  Latency percentiles cover every job: censored jobs count at their cap."""
+    read-back.  Latency percentiles cover every job: censored jobs count at their cap.  The
+    served chains sweep in `order` (0 lexicographic, 1 colour order)."""
     from paper_2011_08560_gb300 import serve
     from paper_2011_08560_gb300.workloads import SERVING
     jobs = serve.poisson_jobs(SERVING["rate_hz"], window_s, SERVING["Ls"], SERVING["rt_min"],
                               SERVING["rt_max"], seed=SERVING["seed"], iter_steps=8, ticks_per_step=8,
                               max_prod_ticks=2000, max_requeues=4)
     server = serve.Server(seed=SERVING["seed"], Ls=SERVING["Ls"], base_sweeps=16, mem_budget=8 << 30,
-                          poll_ticks=8, max_ahead=64)
+                          poll_ticks=8, max_ahead=64, order=order)
     stats = serve.run_poisson(server, jobs, duration_s=window_s, drain_s=drain_s)
     server.close()
     stats["workload"] = (f"Poisson {SERVING['rate_hz']:.0f} jobs/s for {window_s:.0f} s, L in 4..12, "
                          f"round-trip targets log-uniform [10, 1000], power law + Berg, 8 x 8 iteration "
                          f"ticks, production cap 2000 ticks (16 sweeps per tick at L=12, (12/L)^3 times "
-                         f"more at smaller L)")
+                         f"more at smaller L), sites in the {'colour' if order else 'lexicographic'} order")
     return stats
 
 
@@ -1050,7 +1051,7 @@ def main():
     if args.only:
         fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
               "uneven": bench_uneven, "uneven_checkerboard": lambda: bench_uneven(order=1),
-              "serving": bench_serving,
+              "serving": bench_serving, "serving_colour": lambda: bench_serving(order=1),
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "scan_checkerboard": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps,
                                                               order=1),

@@ -363,8 +363,8 @@ int pt_adapt(ea_ctx *ctx, double eta);
  * the switch to production, requeue, completion).  The host never waits for a tick: finished
  * jobs are read back asynchronously every poll_ticks ticks.  A job's schedule is counted in its
  * own ticks and its random numbers are keyed by its own sweep counter, so its result is the same
- * alone and among other jobs.  Served chains sweep in the lexicographic order.  A server is not
- * thread-safe. */
+ * alone and among other jobs.  Served chains sweep in the configured order (sweep_order).  A
+ * server is not thread-safe. */
 typedef struct ea_srv ea_srv;
 
 typedef struct {
@@ -375,6 +375,7 @@ typedef struct {
                               * base_sweeps * round((L_max / L)^3), about equal work per tick */
     int32_t poll_ticks;      /* ticks between completion read-backs */
     int32_t max_ahead;       /* ticks queued at most beyond the last completed read-back */
+    int32_t sweep_order;     /* EA_ORDER_LEX (0) or EA_ORDER_COLOUR (1), see muca_set_sweep_order */
 } ea_srv_config;
 
 /* One job: realization rid (couplings and initial spins drawn from the server's seed, as

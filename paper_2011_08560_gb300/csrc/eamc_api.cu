@@ -667,7 +667,9 @@ static int colour_launch(ea_ctx *ctx, int *C_out, size_t *smem_out, size_t *ck_s
     }
 }
 
-static int enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
+// the context's sweeps in its order and launch configuration, queued on its stream (also the
+// serving loop's tick in the colour order)
+int ctx_enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
     const int nt = (int)ctx->tiles.size();
     const uint64_t chunk = ctx->sweeps_per_launch ? ctx->sweeps_per_launch : n_sweeps;
     if (ctx->order == 1) {
@@ -713,7 +715,7 @@ extern "C" int muca_run_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtr
     for (const TileDesc &td : ctx->tiles) mul = std::max<uint64_t>(mul, (uint64_t)td.sweep_mul);
     if (n_sweeps > (1ull << 32) || ctx->max_t_host + n_sweeps * mul > (1ull << 32))
         return fail(EA_EINVAL, "sweep counter would exceed 2^32");
-    int rc = enqueue_sweeps(ctx, n_sweeps, count_roundtrips);
+    int rc = ctx_enqueue_sweeps(ctx, n_sweeps, count_roundtrips);
     if (rc) return rc;
     ctx->max_t_host += n_sweeps * mul;
     return EA_OK;
@@ -787,7 +789,7 @@ extern "C" int ea_graph_capture(ea_ctx *ctx, int n_iter, uint64_t sweeps_per_ite
     int rc = EA_OK;
     const int nt = (int)ctx->tiles.size();
     for (int it = 0; it < n_iter && rc == EA_OK; ++it) {
-        rc = enqueue_sweeps(ctx, sweeps_per_iter, count_roundtrips);
+        rc = ctx_enqueue_sweeps(ctx, sweeps_per_iter, count_roundtrips);
         if (rc == EA_OK && update_weights) {
             cudaError_t e = launch_update_weights(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_hist, ctx->d_acc, ctx->stream);
             if (e == cudaSuccess) e = launch_quantize(ctx->d_tiles, nt, ctx->d_slots, ctx->d_lnW, ctx->d_thr, ctx->stream);

@@ -71,5 +71,6 @@ int ctx_refresh_chains(ea_ctx *ctx);
 int ctx_rebuild_order(ea_ctx *ctx);
 void ctx_drop_graph(ea_ctx *ctx);
 }  // namespace eamc
+int ctx_enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips);
 
 void pt_release(ea_ctx *ctx);

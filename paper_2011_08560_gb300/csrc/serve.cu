@@ -319,9 +319,15 @@ int admit(ea_srv *s) {
 int enqueue_tick(ea_srv *s) {
     ea_ctx *c = s->ctx;
     const int nt = (int)c->tiles.size(), ns = nt * kTile;
-    cudaError_t e = launch_sweeps(c->d_tiles, nullptr, nt, nt, nullptr, c->dim, c->sweep_smem, c->d_slots, c->d_spins,
-                                  c->d_bonds, c->d_thr, c->d_hist, (uint64_t)s->base_sweeps, c->key, 1,
-                                  reinterpret_cast<unsigned *>(c->d_queue + 1), s->st);
+    cudaError_t e = cudaSuccess;
+    if (c->order == EA_ORDER_COLOUR) {  // the context's colour-order kernels (both parities)
+        const int rc = ctx_enqueue_sweeps(c, (uint64_t)s->base_sweeps, 1);
+        if (rc) return rc;
+    } else {
+        e = launch_sweeps(c->d_tiles, nullptr, nt, nt, nullptr, c->dim, c->sweep_smem, c->d_slots, c->d_spins,
+                          c->d_bonds, c->d_thr, c->d_hist, (uint64_t)s->base_sweeps, c->key, 1,
+                          reinterpret_cast<unsigned *>(c->d_queue + 1), s->st);
+    }
     if (e == cudaSuccess)
         e = launch_srv_control(c->d_tiles, ns, c->d_slots, s->d_ctl, s->d_flag, s->d_ring, s->d_head, kRingCap,
                                s->d_attempts, s->ticks + 1, s->st);
@@ -341,6 +347,8 @@ extern "C" int ea_srv_create(ea_srv **out, int device, void *cuda_stream, uint64
     if (cfg->n_L <= 0 || cfg->n_L > 16) return fail(EA_EINVAL, "n_L must be in [1, 16]");
     if (cfg->base_sweeps <= 0 || cfg->poll_ticks <= 0 || cfg->max_ahead < cfg->poll_ticks)
         return fail(EA_EINVAL, "need base_sweeps > 0, poll_ticks > 0, max_ahead >= poll_ticks");
+    if (cfg->sweep_order != EA_ORDER_LEX && cfg->sweep_order != EA_ORDER_COLOUR)
+        return fail(EA_EINVAL, "unknown sweep order %d", cfg->sweep_order);
     ea_srv *s = new ea_srv();
     s->device = device;
     s->dim = cfg->dim;
@@ -360,6 +368,7 @@ extern "C" int ea_srv_create(ea_srv **out, int device, void *cuda_stream, uint64
     s->t0 = std::chrono::steady_clock::now();
     int rc = ea_create(&s->ctx, device, cuda_stream, seed);
     if (rc) { delete s; return rc; }
+    if ((rc = muca_set_sweep_order(s->ctx, cfg->sweep_order, 0))) { ea_destroy(s->ctx); delete s; return rc; }
     bool ok = cudaMalloc(&s->d_ring, kRingCap * sizeof(SrvRecord)) == cudaSuccess &&
               cudaMalloc(&s->d_head, sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&s->d_attempts, sizeof(unsigned long long)) == cudaSuccess &&

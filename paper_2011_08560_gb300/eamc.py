@@ -54,7 +54,7 @@ class ea_pt_stats(ctypes.Structure):
 class ea_srv_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_L", ctypes.c_int32), ("Ls", ctypes.c_int32 * 16),
                 ("mem_budget", ctypes.c_size_t), ("base_sweeps", ctypes.c_int32),
-                ("poll_ticks", ctypes.c_int32), ("max_ahead", ctypes.c_int32)]
+                ("poll_ticks", ctypes.c_int32), ("max_ahead", ctypes.c_int32), ("sweep_order", ctypes.c_int32)]
 
 
 class ea_job(ctypes.Structure):

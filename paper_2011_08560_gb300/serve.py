@@ -70,13 +70,15 @@ class Server:
 
     def __init__(self, seed: int, Ls=(4, 5, 6, 7, 8, 9, 10, 11, 12), dim: int = 3,
                  mem_budget: int = 2 << 30, base_sweeps: int = 8, poll_ticks: int = 8,
-                 max_ahead: int = 64, stream=None, device: int = 0):
+                 max_ahead: int = 64, stream=None, device: int = 0, order: int = 0):
+        """order: the sites' order within a sweep for every served chain (eamc.EA_ORDER_LEX or
+        eamc.EA_ORDER_COLOUR)."""
         import torch
         self.stream = stream or torch.cuda.Stream(device=device)
-        self.dim, self.Ls, self.base_sweeps = dim, tuple(Ls), base_sweeps
+        self.dim, self.Ls, self.base_sweeps, self.order = dim, tuple(Ls), base_sweeps, order
         self.mem_budget = mem_budget
         cfg = eamc.ea_srv_config(dim=dim, n_L=len(self.Ls), mem_budget=mem_budget, base_sweeps=base_sweeps,
-                                 poll_ticks=poll_ticks, max_ahead=max_ahead)
+                                 poll_ticks=poll_ticks, max_ahead=max_ahead, sweep_order=order)
         for k, L in enumerate(self.Ls):
             cfg.Ls[k] = L
         self._h = ctypes.c_void_p()

@@ -58,9 +58,9 @@ def test_same_result_alone_and_in_mix(serve):
     assert a.result["n_rt"] >= 6
 
 
-def _oracle_replay(orc, seed, job, spt):
+def _oracle_replay(orc, seed, job, spt, order=0):
     """The job's schedule in the oracle, tick by tick (the device's job control)."""
-    ch = orc.Chain(3, job.L, seed, job.rid, job.stream)
+    ch = orc.Chain(3, job.L, seed, job.rid, job.stream, order=order)
     lnW = np.zeros(ch.b_top + 1)
     acc = orc.berg_state(ch.b_top + 1)
     kind = orc.POWERLAW if job.kind == 1 else orc.FLAT
@@ -107,11 +107,14 @@ def _oracle_replay(orc, seed, job, spt):
                     "e_min": ch.rt.e_min, "sweeps": ch.t, "requeues": requeues}
 
 
-@pytest.mark.parametrize("L,recursion,target", [(4, 1, 5), (5, 0, 4), (6, 1, 3)])
-def test_served_job_matches_oracle_replay(serve, orc, L, recursion, target):
+@pytest.mark.parametrize("L,recursion,target,order", [(4, 1, 5, 0), (5, 0, 4, 0), (6, 1, 3, 0),
+                                                     (4, 1, 5, 1), (5, 0, 4, 1), (6, 1, 3, 1)])
+def test_served_job_matches_oracle_replay(serve, orc, L, recursion, target, order):
     """Power-law jobs whose weight steps leave E_g above the ground state, so that production
-    finds lower energies and requeues (new E_g, one more step, counting restarts)."""
-    srv = serve.Server(seed=41, Ls=(4, 5, 6), base_sweeps=2)
+    finds lower energies and requeues (new E_g, one more step, counting restarts); served in
+    the lexicographic and in the colour order (checkerboard kernel for even L, warp-per-chain
+    kernel for odd L)."""
+    srv = serve.Server(seed=41, Ls=(4, 5, 6), base_sweeps=2, order=order)
     jobs = [_job(serve, k, L, 300 + k, target, recursion=recursion, iter_steps=1, ticks_per_step=2,
                  max_prod_ticks=4000, max_requeues=3) for k in range(6)]
     for j in jobs:
@@ -122,7 +125,7 @@ def test_served_job_matches_oracle_replay(serve, orc, L, recursion, target):
     srv.close()
     requeued = 0
     for j in jobs:
-        status, want = _oracle_replay(orc, 41, j, spt)
+        status, want = _oracle_replay(orc, 41, j, spt, order)
         assert j.phase == status, (j.jid, j.phase, status)
         for k in RESULT_KEYS:
             assert j.result[k] == want[k], (j.jid, k, j.result[k], want[k])
