@@ -157,15 +157,14 @@ int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch, int
  *   c(x) = x mod 3 except c(L-1) = 1 when L = 1 (mod 3)), each in lexicographic order; the
  *   j-th colour-c site of a row takes word j&3 of call (4 row + j/4, t, rid, (5 + c) | stream << 8).
  *   No two sites of a class are neighbours, so each attempt's class is fixed when its class
- *   begins.  Even L runs one lane per chain in the tiles of the lexicographic kernel (the tile
- *   widths of muca_set_tile_width apply) and needs one candidate-threshold pair per attempt
- *   instead of two classes' worth: the faster order for even L up to 8.  Odd L runs one warp per
- *   chain, resolving the attempts of a pass four at a time from acceptance ballots over the
- *   reachable bins.
- * chains_per_cta (colour order, odd L only): warps (chains) per thread block, 1, 2, 4 or 8, or 0
- * to choose per launch (the largest that still gives every SM a block).  Applies from the next
- * muca_run_sweeps or graph capture; the order is not part of a snapshot.  EA_EINVAL for an
- * unknown order or count. */
+ *   begins.  One kernel runs it for every L, one lane per chain in the tiles of the lexicographic
+ *   kernel (the tile widths of muca_set_tile_width apply; odd L has three colour passes and
+ *   rows with different numbers of colour sites, padded with attempts that move nothing): one
+ *   candidate-threshold pair per attempt instead of two classes' worth, the faster order for
+ *   L <= 8.
+ * chains_per_cta: 0 or one of 1, 2, 4, 8 (kept for callers of an earlier form of this call; it
+ * has no effect).  Applies from the next muca_run_sweeps or graph capture; the order is not part
+ * of a snapshot.  EA_EINVAL for an unknown order or count. */
 int muca_set_sweep_order(ea_ctx *ctx, int order, int chains_per_cta);
 
 /* a8 -- chains per tile for chains of linear size L added afterwards (ea_init_disorder):

@@ -629,42 +629,17 @@ extern "C" int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g) {
     return EA_OK;
 }
 
-// The colour order runs in two kernels: even L (the checkerboard) with one lane per chain in
-// the tiles of the lexicographic kernel, odd L with one warp per chain.  Each launch skips the
-// other parity's tiles.  colour_launch: chains per CTA of the odd-L kernel and its shared
-// memory (the requested C, or the largest C <= 8 whose grid still covers every SM, halved until
-// the largest odd lattice fits; C = 0: no odd tiles) and the even-L kernel's shared memory
-// (0: no even tiles).
-static int colour_launch(ea_ctx *ctx, int *C_out, size_t *smem_out, size_t *ck_smem_out) {
+// The colour order runs in the checkerboard kernel (every L: one lane per chain in the tiles of
+// the lexicographic kernel, three colour passes for odd L); its shared memory for the context's
+// tiles.
+static int colour_launch(ea_ctx *ctx, size_t *ck_smem_out) {
     int optin = 0;
     EA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     size_t ck = 0;
-    int n_odd = 0;
-    for (const TileDesc &td : ctx->tiles) {
-        if (td.L & 1) ++n_odd;
-        else ck = std::max(ck, checker_smem_bytes(td.dim, td.L, td.width));
-    }
-    if (ck > (size_t)optin) return fail(EA_EINVAL, "the checkerboard sweep does not fit in shared memory");
+    for (const TileDesc &td : ctx->tiles) ck = std::max(ck, checker_smem_bytes(td.dim, td.L, td.width));
+    if (ck > (size_t)optin) return fail(EA_EINVAL, "the colour-order sweep does not fit in shared memory");
     *ck_smem_out = ck;
-    *C_out = 0;
-    *smem_out = 0;
-    if (n_odd == 0) return EA_OK;
-    int C = ctx->colour_C;
-    if (C <= 0) {
-        C = 8;
-        while (C > 1 && (size_t)n_odd * (32 / C) < (size_t)std::max(ctx->n_sm, 1)) C /= 2;
-    }
-    for (;; C /= 2) {
-        size_t smem = 0;
-        for (const TileDesc &td : ctx->tiles)
-            if (td.L & 1) smem = std::max(smem, colour_smem_bytes(td.dim, td.L, C));
-        if (smem <= (size_t)optin) {
-            *C_out = C;
-            *smem_out = smem;
-            return EA_OK;
-        }
-        if (C == 1) return fail(EA_EINVAL, "the colour-order sweep does not fit in shared memory");
-    }
+    return EA_OK;
 }
 
 // the context's sweeps in its order and launch configuration, queued on its stream (also the
@@ -673,20 +648,15 @@ int ctx_enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
     const int nt = (int)ctx->tiles.size();
     const uint64_t chunk = ctx->sweeps_per_launch ? ctx->sweeps_per_launch : n_sweeps;
     if (ctx->order == 1) {
-        int C = 0, rc;
-        size_t smem = 0, ck_smem = 0;
-        if ((rc = colour_launch(ctx, &C, &smem, &ck_smem))) return rc;
+        int rc;
+        size_t ck_smem = 0;
+        if ((rc = colour_launch(ctx, &ck_smem))) return rc;
         unsigned *diag = reinterpret_cast<unsigned *>(ctx->d_queue + 1);
-        for (uint64_t done = 0; done < n_sweeps; done += chunk) {
+        for (uint64_t done = 0; done < n_sweeps && ck_smem > 0; done += chunk) {
             const uint64_t now = std::min(chunk, n_sweeps - done);
-            if (ck_smem > 0)
-                EA_CUDA(launch_sweeps_checker(ctx->d_tiles, nt, ctx->dim, ck_smem, ctx->d_slots, ctx->d_spins,
-                                              ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key,
-                                              count_roundtrips, diag, ctx->stream));
-            if (C > 0)
-                EA_CUDA(launch_sweeps_colour(ctx->d_tiles, nt, C, ctx->dim, smem, ctx->d_slots, ctx->d_spins,
-                                             ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key, count_roundtrips,
-                                             diag, ctx->stream));
+            EA_CUDA(launch_sweeps_checker(ctx->d_tiles, nt, ctx->dim, ck_smem, ctx->d_slots, ctx->d_spins,
+                                          ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key, count_roundtrips,
+                                          diag, ctx->stream));
         }
         return EA_OK;
     }
@@ -743,7 +713,7 @@ extern "C" int muca_set_sweep_order(ea_ctx *ctx, int order, int chains_per_cta) 
     if (chains_per_cta != 0 && (chains_per_cta < 1 || chains_per_cta > 8 || (32 % chains_per_cta) != 0))
         return fail(EA_EINVAL, "chains_per_cta must be 0 or one of 1, 2, 4, 8");
     ctx->order = order;
-    ctx->colour_C = chains_per_cta;
+    (void)chains_per_cta;  // no effect: the colour order runs one lane per chain at every L
     return EA_OK;
 }
 

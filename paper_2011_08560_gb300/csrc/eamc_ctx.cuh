@@ -48,7 +48,6 @@ struct ea_ctx {
     int blocks_per_sm = 0;            // persistent grid: resident blocks per SM (0: occupancy limit)
     int tile_width[13] = {32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32};  // chains per tile by L
     int order = 0;                    // sweep order: 0 lexicographic, 1 colour class by colour class
-    int colour_C = 0;                 // colour order: chains (warps) per CTA, 0 = chosen per launch
     int n_sm = 0;
     int32_t *d_order = nullptr;       // tile ids, longest tiles first
     size_t order_cap = 0;

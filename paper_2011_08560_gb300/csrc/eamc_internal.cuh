@@ -106,17 +106,12 @@ cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, i
                           const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
                           PhiloxKey key, int count_rt, unsigned *d_diag, cudaStream_t st);
 int sweep_blocks_per_sm(int dim, size_t smem);
-// the colour-order sweep: even L (the checkerboard) one lane per chain (muca_checker.cu), odd L
-// CTAs of C warps, one warp per chain (muca_colour.cu)
+// the colour-order sweep (muca_checker.cu): one lane per chain, every L
 size_t checker_smem_bytes(int dim, int L, int width);
 cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,
                                   uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr,
                                   uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
                                   unsigned *d_diag, cudaStream_t st);
-size_t colour_smem_bytes(int dim, int L, int C);
-cudaError_t launch_sweeps_colour(const TileDesc *d_tiles, int n_tiles, int C, int dim, size_t smem, SlotState *d_slots,
-                                 uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist,
-                                 uint64_t n_sweeps, PhiloxKey key, int count_rt, unsigned *d_diag, cudaStream_t st);
 cudaError_t prepare_sweeps(int dim, size_t smem);  // resident sweep blocks per SM at this smem
 cudaError_t launch_quantize(const TileDesc *d_tiles, int n_tiles, const SlotState *d_slots,
                             const double *d_lnW, uint32_t *d_thr, cudaStream_t st);

@@ -1,7 +1,9 @@
-// muca_checker.cu -- a2 + a3 in the colour order for even L (the checkerboard): the
+// muca_checker.cu -- a2 + a3 in the colour order (the checkerboard for even L): the
 // multicanonical sweep (Sec. II, Eq. "muca") with the sites of a sweep taken colour by colour,
 // each colour in lexicographic order, for 32 (or 16) independent chains per tile, one lane per
-// chain.
+// chain.  Odd L (three colours, the PT colouring) runs in the same kernel: a row has a varying
+// number of sites of a colour, so each row gets the largest number of attempt slots and the
+// unused ones are padding that moves nothing and never accepts.
 //
 // In a colour pass no two attempted sites are neighbours, so the class n of every attempt
 // (unsatisfied bonds, the move changes the bin by dim - n) is fixed when the pass begins.  The
@@ -66,19 +68,39 @@ __device__ __forceinline__ T ck_prev(T r) {
     return ((r << 4) | (r >> (4 * L - 4))) & ck_mask<T, L>();
 }
 
+// odd L: the colour of a site is (ax(x) + ax(y) + ax(z)) mod 3 with ax(c) = c mod 3, except
+// ax(L-1) = 1 when L - 1 is a multiple of 3 (the PT colouring); the colour-c sites of a row with
+// (c - ax(y) - ax(z)) mod 3 = s are the x with ax(x) = s
+__host__ __device__ constexpr int ck_ax(int L, int c) { return (c == L - 1 && (L - 1) % 3 == 0) ? 1 : c % 3; }
+__host__ __device__ constexpr int ck_sites_max(int L) {  // most colour-c sites in one row
+    int m = 0;
+    for (int s = 0; s < 3; ++s) {
+        int n = 0;
+        for (int x = 0; x < L; ++x) n += ck_ax(L, x) == s;
+        m = n > m ? n : m;
+    }
+    return m;
+}
+
 template <int DIM, int L, int W>
 struct CkGeo {
-    static_assert((L & 1) == 0, "the checkerboard needs even L");
     static_assert(W == 32 || W == 16, "tile width");
     using T = CkRow<L>;
-    static constexpr int NR = DIM == 3 ? L * L : L;  // rows along x (even)
+    static constexpr int NCOL = (L & 1) ? 3 : 2;    // colour passes per sweep
+    static constexpr int NR = DIM == 3 ? L * L : L;  // rows along x
     static constexpr int V = NR * L;
     static constexpr int B = ((DIM * V) / 2 >> 1) + 1;
-    static constexpr int HALF = L / 2;              // colour sites per row
+    // attempt slots per row: the colour-c sites of a row, the last ones padding where the row has
+    // fewer (odd L: a padding slot moves nothing and never accepts)
+    static constexpr int HALF = (L & 1) ? ck_sites_max(L) : L / 2;
+    static_assert(HALF <= 4 || (L & 1) == 0, "one Philox call per row and pass for odd L");
     static constexpr int NGC = (HALF + 3) / 4;      // Philox calls per row and pass
-    static constexpr int RPR = (NR % 4 == 0 && L <= 8) ? 4 : 2;  // rows per record
+    // rows per record: even L four where the rows divide into fours, up to L = 8, else two; odd
+    // L a plane's L rows (the whole lattice for 2D and L = 3) up to L = 9, else two, the last
+    // record of a pass padded with rows of padding slots
+    static constexpr int RPR = (L & 1) ? (L <= 9 ? (NR <= 9 ? NR : L) : 2) : ((NR % 4 == 0 && L <= 8) ? 4 : 2);
     static constexpr int NA = RPR * HALF;           // attempts per record
-    static constexpr int NP = NR / RPR;             // records per pass
+    static constexpr int NP = (NR + RPR - 1) / RPR;  // records per pass
     static constexpr int OW = (HALF + 1) / 2;       // 32-bit words of 16-bit class offsets per row
     static constexpr int OFFQ = (RPR * OW + 3) / 4; // uint4 slots of class offsets (row h at word h * OW)
     static constexpr int HQ = OFFQ + RPR * NGC;     // uint4 slots per lane per record
@@ -112,7 +134,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     using G = CkGeo<DIM, L, W>;
     using T = typename G::T;
     constexpr int NR = G::NR, NP = G::NP, HALF = G::HALF, NGC = G::NGC, LAG = G::LAG, NBUF = G::NBUF;
-    constexpr int RPR = G::RPR, NA = G::NA;
+    constexpr int RPR = G::RPR, NA = G::NA, NCOL = G::NCOL;
+    constexpr bool ODD = (L & 1) != 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ln = lane & (W - 1);  // chain of this lane; lanes ln + W, ... mirror it
     const bool owner = lane < W;
@@ -123,6 +146,32 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     T *JZs = Rs + 3 * NR * W;                 // bond (z, z+1)  (DIM == 3)
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
     int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2 records][NA][W]
+    // odd L: for each colour shift s, the row's colour sites as a byte list (x positions, 0xFF
+    // for padding slots) and their number
+    __shared__ uint32_t s_xs[3];
+    __shared__ int s_ns[3];
+    if constexpr (ODD) {
+        if (threadIdx.x < 3) {
+            const int sh = threadIdx.x;
+            uint32_t pk = 0xFFFFFFFFu;
+            int n = 0;
+            for (int x = 0; x < L; ++x) {
+                if (ck_ax(L, x) == sh) {
+                    pk = (pk & ~(0xFFu << (8 * n))) | ((uint32_t)x << (8 * n));
+                    ++n;
+                }
+            }
+            s_xs[sh] = pk;
+            s_ns[sh] = n;
+        }
+    }
+    // the colour shift of row r in pass c: its colour sites are x0 + 2j (even L, x0 = the shift)
+    // or the list of shift s (odd L)
+    auto row_shift = [](int c, int r) -> int {
+        const int y = r % L, z = DIM == 3 ? r / L : 0;
+        if constexpr (ODD) return ((c - ck_ax(L, y) - (DIM == 3 ? ck_ax(L, z) : 0)) % 3 + 3) % 3;
+        else return (c + y + z) & 1;
+    };
     const uint32_t *gsp = spins + td.spin_off;
     const uint32_t *gbd = bonds + td.bond_off;
     for (int row = warp; row < NR; row += kCkWarps) {
@@ -173,7 +222,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
         tab = reinterpret_cast<const char *>(thr + lrow * 8);
     }
     const uint64_t t0 = ss.t;
-    const uint64_t n_pass = n_sweeps * 2;  // colour passes
+    const uint64_t n_pass = n_sweeps * NCOL;  // colour passes
 
     __syncthreads();
     // Every warp passes the same barriers: one after staging, per pass one fill barrier and NP
@@ -183,19 +232,26 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
         auto produce = [&](int c, int p, uint32_t t, int k) {
             uint4 *buf = hand + k * G::HQ * W;
             const int r0 = RPR * p;
-            const int h0 = warp >= 4 ? RPR / 2 : 0;  // this warp prepares rows h0 .. h0 + RPR/2 - 1 of the record
-            if (ck_random(warp)) {  // clamped as in the lexicographic kernel
+            // this warp prepares rows h0 .. h1 - 1 of the record (the first warp of a role one more
+            // for odd RPR)
+            const int h0 = warp >= 4 ? (RPR + 1) / 2 : 0, h1 = warp >= 4 ? RPR : (RPR + 1) / 2;
+            if (ck_random(warp)) {  // clamped as in the lexicographic kernel; padding: never accepts
                 const uint32_t c3 = (uint32_t)(5 + c) | (ss.stream << 8);
 #pragma unroll
-                for (int h = h0; h < h0 + RPR / 2; ++h) {
+                for (int h = h0; h < h1; ++h) {
                     const int r = r0 + h;
+                    const int nreal = r >= NR ? 0 : (ODD ? s_ns[row_shift(c, r)] : HALF);  // uniform
 #pragma unroll
                     for (int g = 0; g < NGC; ++g) {
-                        uint4 w = philox4x32_10(make_uint4((uint32_t)(4 * r + g), t, ss.rid, c3), key);
-                        w.x = active ? min(w.x, kAlways - 1u) : kAlways;
-                        w.y = active ? min(w.y, kAlways - 1u) : kAlways;
-                        w.z = active ? min(w.z, kAlways - 1u) : kAlways;
-                        w.w = active ? min(w.w, kAlways - 1u) : kAlways;
+                        uint4 w = make_uint4(kAlways, kAlways, kAlways, kAlways);
+                        if (4 * g < nreal) {
+                            w = philox4x32_10(make_uint4((uint32_t)(4 * r + g), t, ss.rid, c3), key);
+                            const bool ok = active;
+                            w.x = (ok && 4 * g + 0 < nreal) ? min(w.x, kAlways - 1u) : kAlways;
+                            w.y = (ok && 4 * g + 1 < nreal) ? min(w.y, kAlways - 1u) : kAlways;
+                            w.z = (ok && 4 * g + 2 < nreal) ? min(w.z, kAlways - 1u) : kAlways;
+                            w.w = (ok && 4 * g + 3 < nreal) ? min(w.w, kAlways - 1u) : kAlways;
+                        }
                         buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
                     }
                 }
@@ -204,10 +260,21 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             // classes of row h (nibble 2j of s: the j-th colour site), stored as table offsets
             // n * NSB, 16 bits per attempt, the row's offsets from word h * OW
 #pragma unroll
-            for (int h = h0; h < h0 + RPR / 2; ++h) {
+            for (int h = h0; h < h1; ++h) {
+            const int r = r0 + h;
+            if (r >= NR) {  // padding row: class dim in every slot (no move)
+#pragma unroll
+                for (int q = 0; q < G::OW; ++q) {
+                    const int wd = h * G::OW + q;
+                    reinterpret_cast<uint32_t *>(buf + (wd >> 2) * W + ln)[wd & 3] =
+                        (uint32_t)(DIM * NSB) * 0x00010001u;
+                }
+                continue;
+            }
             T s;
+            uint32_t xs = 0u;  // odd L: the row's colour sites (bytes, 0xFF padding)
             {
-                const int r = r0 + h, y = r % L, z = DIM == 3 ? r / L : 0;
+                const int y = r % L, z = DIM == 3 ? r / L : 0;
                 const T R = Rs[r * W + ln];
                 const T uxp = R ^ ck_next<T, L>(R) ^ JXs[r * W + ln];
                 const int ryp = (y == L - 1) ? r - (L - 1) : r + 1;
@@ -219,15 +286,25 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                     const int rzm = (z == 0) ? r + (L - 1) * L : r - L;
                     sum += (R ^ Rs[rzp * W + ln] ^ JZs[r * W + ln]) + (R ^ Rs[rzm * W + ln] ^ JZs[rzm * W + ln]);
                 }
-                const int x0 = (c + y + z) & 1;  // first colour-c site of the row
-                s = sum >> (4 * x0);
+                if constexpr (ODD) {
+                    s = sum;
+                    xs = s_xs[row_shift(c, r)];
+                } else {
+                    s = sum >> (4 * row_shift(c, r));  // nibble 2j: the j-th colour site
+                }
             }
             uint32_t off[G::OW];
 #pragma unroll
             for (int q = 0; q < G::OW; ++q) off[q] = 0u;
 #pragma unroll
             for (int j = 0; j < HALF; ++j) {
-                const uint32_t n = (uint32_t)((s >> (8 * j)) & 0xF);
+                uint32_t n;
+                if constexpr (ODD) {
+                    const uint32_t x = (xs >> (8 * j)) & 0xFFu;
+                    n = x == 0xFFu ? (uint32_t)DIM : (uint32_t)((s >> (4 * x)) & 0xF);
+                } else {
+                    n = (uint32_t)((s >> (8 * j)) & 0xF);
+                }
                 off[j >> 1] |= (n * NSB) << (16 * (j & 1));
             }
 #pragma unroll
@@ -260,7 +337,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             }
             pmin = min(pmin, lo);
             out_of_range |= (lo < 0) | (hi > topB);
-            const uint64_t sweep = mrec / (2 * NP);
+            const uint64_t sweep = mrec / (NCOL * NP);
             if (count_rt && active && ((phase == 1) ? mbot : mtop) != 0u) {
                 const int64_t t = (int64_t)(t0 + sweep);
                 int a0 = 0;
@@ -273,12 +350,12 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                     else { nrt += 1; tl = t; phase = 1; }
                 }
             }
-            if (++mrec % (2 * NP) == 0 && active && owner) atomicAdd(&hist[lrow + pnow / RSB], 1u);
+            if (++mrec % (NCOL * NP) == 0 && active && owner) atomicAdd(&hist[lrow + pnow / RSB], 1u);
         };
         uint64_t g = 0;  // records the consumer has been given
         for (uint64_t q = 0; q < n_pass; ++q) {
-            const int c = (int)(q & 1);
-            const uint32_t t = (uint32_t)(t0 + (q >> 1));
+            const int c = (int)(q % NCOL);
+            const uint32_t t = (uint32_t)(t0 + q / NCOL);
             __syncthreads();  // fill barrier: the previous pass is complete
             if (warp == kCkMeasure && g > 0) measure(g - 1);
             if (producer)
@@ -323,7 +400,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     };
     uint64_t g = 0;
     for (uint64_t q = 0; q < n_pass; ++q) {
-        const int c = (int)(q & 1);
+        const int c = (int)(q % NCOL);
         __syncthreads();  // fill barrier
         bool have_next = false;
         for (int k = 0; k < NP; ++k, ++g) {
@@ -347,9 +424,18 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             }
             have_next = false;
             int *resb = res + (int)(g & 1) * NA * W + ln;
-            T flipped[RPR];  // bit 8j: the j-th colour site of the row flipped
+            // even L: bit 8j of flipped[h] is the row's j-th colour site (spread at the row's end);
+            // odd L: the site's own nibble, at the shifts fsh of the row's colour sites
+            T flipped[RPR];
+            uint32_t fsh[RPR];
 #pragma unroll
-            for (int h = 0; h < RPR; ++h) flipped[h] = 0;
+            for (int h = 0; h < RPR; ++h) {
+                flipped[h] = 0;
+                if constexpr (ODD) {  // padding bytes (0xFF) become x = 0: they never accept
+                    const uint32_t xs = r0 + h < NR ? s_xs[row_shift(c, r0 + h)] : 0u;
+                    fsh[h] = xs & ~(((xs >> 7) & 0x01010101u) * 0xFFu);
+                }
+            }
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 const int h = a / HALF, j = a % HALF;
@@ -380,7 +466,11 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                 const int rx = pa ? rB : rq;
                 const uint32_t r = uint4_get(rr[h * NGC + (j >> 2)], j & 3);
                 const bool acc = r < th;  // r clamped by the producer
-                flipped[h] |= T(acc ? 1u : 0u) << (8 * j);
+                if constexpr (ODD) {
+                    flipped[h] |= T(acc ? 1u : 0u) << (4 * ((fsh[h] >> (8 * j)) & 0xFu));
+                } else {
+                    flipped[h] |= T(acc ? 1u : 0u) << (8 * j);
+                }
                 resb[a * W] = acc ? rx + dx : rx;  // bin row offset after the attempt, for the measurement
                 rq = rx;
                 dq = dx;
@@ -393,8 +483,11 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             }
 #pragma unroll
             for (int h = 0; h < RPR; ++h) {
-                const int r = r0 + h, x0 = (c + r % L + (DIM == 3 ? r / L : 0)) & 1;
-                Rs[(r0 + h) * W + ln] ^= flipped[h] << (4 * x0);
+                const int r = r0 + h;
+                if (r < NR) {  // padding rows have no spins
+                    if constexpr (ODD) Rs[r * W + ln] ^= flipped[h];
+                    else Rs[r * W + ln] ^= flipped[h] << (4 * row_shift(c, r));
+                }
             }
         }
     }
@@ -419,20 +512,25 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
                     unsigned *__restrict__ diag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileDesc td = tiles[blockIdx.x];
-    if (td.L & 1) return;  // odd L: the warp-per-chain colour kernel (whole CTA, before any barrier)
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CK(LL, WW) checker_tile<DIM, LL, WW>(td, blockIdx.x, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
     if (td.width == 16) {
         if constexpr (DIM == 3) {
-            if (td.L == 8) EAMC_CK(8, 16);
+            if (td.L == 7) EAMC_CK(7, 16);
+            else if (td.L == 8) EAMC_CK(8, 16);
         }
         return;
     }
     switch (td.L) {
+        case 3: EAMC_CK(3, 32); break;
         case 4: EAMC_CK(4, 32); break;
+        case 5: EAMC_CK(5, 32); break;
         case 6: EAMC_CK(6, 32); break;
+        case 7: EAMC_CK(7, 32); break;
         case 8: EAMC_CK(8, 32); break;
+        case 9: EAMC_CK(9, 32); break;
         case 10: EAMC_CK(10, 32); break;
+        case 11: EAMC_CK(11, 32); break;
         case 12: EAMC_CK(12, 32); break;
         default: break;
     }
@@ -442,10 +540,15 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
 template <int DIM, int W>
 size_t checker_smem_w(int L) {
     switch (L) {
+        case 3: return CkGeo<DIM, 3, W>::SMEM;
         case 4: return CkGeo<DIM, 4, W>::SMEM;
+        case 5: return CkGeo<DIM, 5, W>::SMEM;
         case 6: return CkGeo<DIM, 6, W>::SMEM;
+        case 7: return CkGeo<DIM, 7, W>::SMEM;
         case 8: return CkGeo<DIM, 8, W>::SMEM;
+        case 9: return CkGeo<DIM, 9, W>::SMEM;
         case 10: return CkGeo<DIM, 10, W>::SMEM;
+        case 11: return CkGeo<DIM, 11, W>::SMEM;
         case 12: return CkGeo<DIM, 12, W>::SMEM;
         default: return 0;
     }
@@ -454,8 +557,11 @@ size_t checker_smem_w(int L) {
 }  // namespace
 
 size_t checker_smem_bytes(int dim, int L, int width) {
-    if ((L & 1) || L < 4 || L > 12) return 0;
-    if (width == 16) return (dim == 3 && L == 8) ? CkGeo<3, 8, 16>::SMEM : 0;
+    if (L < 3 || L > 12) return 0;
+    if (width == 16) {
+        if (dim != 3) return 0;
+        return L == 7 ? CkGeo<3, 7, 16>::SMEM : (L == 8 ? CkGeo<3, 8, 16>::SMEM : 0);
+    }
     if (width != 32) return 0;
     return dim == 3 ? checker_smem_w<3, 32>(L) : checker_smem_w<2, 32>(L);
 }

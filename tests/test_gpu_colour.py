@@ -1,9 +1,10 @@
 """The colour-order sweep kernels against the oracle's colour order, element by element: spins,
-energies, histograms and round-trip records bit-exact, weights to 1e-12.  Even L runs the
-checkerboard kernel (one lane per chain; records of two or four rows, one or two records of
-look-ahead, 2D and 3D, full and narrow tiles), odd L the warp-per-chain kernel (every block
-size); launch splitting, captured graphs, contexts holding both parities and the weight
-recursions."""
+energies, histograms and round-trip records bit-exact, weights to 1e-12.  One kernel, one lane
+per chain, for every L: even L two colour passes, odd L three with rows padded to the most
+colour sites of a row; records of two or four rows or a plane, one or two records of look-ahead,
+padded last records, 2D and 3D, full and narrow tiles; launch splitting, captured graphs,
+contexts holding both parities and the weight recursions (the chains-per-CTA argument has no
+effect)."""
 import numpy as np
 import pytest
 
@@ -163,7 +164,7 @@ def test_sweep_order_rejects_bad_arguments(eamc):
 def test_colour_snapshot_resume_and_narrow_tiles(eamc, orc):
     """The colour order continues a snapshot bit-exactly (the order is the caller's setting, not
     part of the snapshot): 2 x 30 sweeps straight == 30, snapshot, restore, 30; chains of an even
-    (checkerboard kernel, 16-chain tiles) and an odd size (warp-per-chain kernel) in one context;
+    (16-chain tiles) and an odd size (three colour passes) in one context;
     the oracle's colour order agrees."""
     def make():
         ctx = eamc.Context(seed=SEED)

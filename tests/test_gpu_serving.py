@@ -112,8 +112,7 @@ def _oracle_replay(orc, seed, job, spt, order=0):
 def test_served_job_matches_oracle_replay(serve, orc, L, recursion, target, order):
     """Power-law jobs whose weight steps leave E_g above the ground state, so that production
     finds lower energies and requeues (new E_g, one more step, counting restarts); served in
-    the lexicographic and in the colour order (checkerboard kernel for even L, warp-per-chain
-    kernel for odd L)."""
+    the lexicographic and in the colour order (even and odd L)."""
     srv = serve.Server(seed=41, Ls=(4, 5, 6), base_sweeps=2, order=order)
     jobs = [_job(serve, k, L, 300 + k, target, recursion=recursion, iter_steps=1, ticks_per_step=2,
                  max_prod_ticks=4000, max_requeues=3) for k in range(6)]
