@@ -629,16 +629,21 @@ extern "C" int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g) {
     return EA_OK;
 }
 
-// The colour order runs in the checkerboard kernel (every L: one lane per chain in the tiles of
-// the lexicographic kernel, three colour passes for odd L); its shared memory for the context's
-// tiles.
-static int colour_launch(ea_ctx *ctx, size_t *ck_smem_out) {
+// The colour order runs in the checkerboard kernels (one lane per chain in the tiles of the
+// lexicographic kernel; three colour passes for odd L, a kernel of their own); the shared memory
+// for the context's tiles and which parities occur (bit 0 even, bit 1 odd L).
+static int colour_launch(ea_ctx *ctx, size_t *ck_smem_out, int *parities) {
     int optin = 0;
     EA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     size_t ck = 0;
-    for (const TileDesc &td : ctx->tiles) ck = std::max(ck, checker_smem_bytes(td.dim, td.L, td.width));
+    int par = 0;
+    for (const TileDesc &td : ctx->tiles) {
+        ck = std::max(ck, checker_smem_bytes(td.dim, td.L, td.width));
+        par |= 1 << (td.L & 1);
+    }
     if (ck > (size_t)optin) return fail(EA_EINVAL, "the colour-order sweep does not fit in shared memory");
     *ck_smem_out = ck;
+    *parities = par;
     return EA_OK;
 }
 
@@ -648,15 +653,15 @@ int ctx_enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
     const int nt = (int)ctx->tiles.size();
     const uint64_t chunk = ctx->sweeps_per_launch ? ctx->sweeps_per_launch : n_sweeps;
     if (ctx->order == 1) {
-        int rc;
+        int rc, parities = 0;
         size_t ck_smem = 0;
-        if ((rc = colour_launch(ctx, &ck_smem))) return rc;
+        if ((rc = colour_launch(ctx, &ck_smem, &parities))) return rc;
         unsigned *diag = reinterpret_cast<unsigned *>(ctx->d_queue + 1);
         for (uint64_t done = 0; done < n_sweeps && ck_smem > 0; done += chunk) {
             const uint64_t now = std::min(chunk, n_sweeps - done);
             EA_CUDA(launch_sweeps_checker(ctx->d_tiles, nt, ctx->dim, ck_smem, ctx->d_slots, ctx->d_spins,
                                           ctx->d_bonds, ctx->d_thr, ctx->d_hist, now, ctx->key, count_roundtrips,
-                                          diag, ctx->stream));
+                                          diag, ctx->stream, parities));
         }
         return EA_OK;
     }

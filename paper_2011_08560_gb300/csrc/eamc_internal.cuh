@@ -111,7 +111,7 @@ size_t checker_smem_bytes(int dim, int L, int width);
 cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,
                                   uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr,
                                   uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
-                                  unsigned *d_diag, cudaStream_t st);
+                                  unsigned *d_diag, cudaStream_t st, int parities);  // bit 0 even L, bit 1 odd L
 cudaError_t prepare_sweeps(int dim, size_t smem);  // resident sweep blocks per SM at this smem
 cudaError_t launch_quantize(const TileDesc *d_tiles, int n_tiles, const SlotState *d_slots,
                             const double *d_lnW, uint32_t *d_thr, cudaStream_t st);

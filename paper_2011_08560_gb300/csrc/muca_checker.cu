@@ -136,6 +136,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     constexpr int NR = G::NR, NP = G::NP, HALF = G::HALF, NGC = G::NGC, LAG = G::LAG, NBUF = G::NBUF;
     constexpr int RPR = G::RPR, NA = G::NA, NCOL = G::NCOL;
     constexpr bool ODD = (L & 1) != 0;
+    constexpr bool PADROWS = (NR % RPR) != 0;  // the last record of a pass has rows of padding (odd L only)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ln = lane & (W - 1);  // chain of this lane; lanes ln + W, ... mirror it
     const bool owner = lane < W;
@@ -233,26 +234,41 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             uint4 *buf = hand + k * G::HQ * W;
             const int r0 = RPR * p;
             // this warp prepares rows h0 .. h1 - 1 of the record (the first warp of a role one more
-            // for odd RPR)
-            const int h0 = warp >= 4 ? (RPR + 1) / 2 : 0, h1 = warp >= 4 ? RPR : (RPR + 1) / 2;
+            // for odd RPR); loops of RH iterations with a guard keep the trip count a constant
+            constexpr int RH = (RPR + 1) / 2;
+            const int h0 = warp >= 4 ? RH : 0, h1 = warp >= 4 ? RPR : RH;
             if (ck_random(warp)) {  // clamped as in the lexicographic kernel; padding: never accepts
                 const uint32_t c3 = (uint32_t)(5 + c) | (ss.stream << 8);
 #pragma unroll
-                for (int h = h0; h < h1; ++h) {
+                for (int hi = 0; hi < RH; ++hi) {
+                    const int h = h0 + hi;
+                    if ((RPR & 1) && h >= h1) break;
                     const int r = r0 + h;
-                    const int nreal = r >= NR ? 0 : (ODD ? s_ns[row_shift(c, r)] : HALF);  // uniform
+                    if constexpr (!ODD && !PADROWS) {  // every slot is a site
 #pragma unroll
-                    for (int g = 0; g < NGC; ++g) {
-                        uint4 w = make_uint4(kAlways, kAlways, kAlways, kAlways);
-                        if (4 * g < nreal) {
-                            w = philox4x32_10(make_uint4((uint32_t)(4 * r + g), t, ss.rid, c3), key);
-                            const bool ok = active;
-                            w.x = (ok && 4 * g + 0 < nreal) ? min(w.x, kAlways - 1u) : kAlways;
-                            w.y = (ok && 4 * g + 1 < nreal) ? min(w.y, kAlways - 1u) : kAlways;
-                            w.z = (ok && 4 * g + 2 < nreal) ? min(w.z, kAlways - 1u) : kAlways;
-                            w.w = (ok && 4 * g + 3 < nreal) ? min(w.w, kAlways - 1u) : kAlways;
+                        for (int g = 0; g < NGC; ++g) {
+                            uint4 w = philox4x32_10(make_uint4((uint32_t)(4 * r + g), t, ss.rid, c3), key);
+                            w.x = active ? min(w.x, kAlways - 1u) : kAlways;
+                            w.y = active ? min(w.y, kAlways - 1u) : kAlways;
+                            w.z = active ? min(w.z, kAlways - 1u) : kAlways;
+                            w.w = active ? min(w.w, kAlways - 1u) : kAlways;
+                            buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
                         }
-                        buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
+                    } else {
+                        const int nreal = r >= NR ? 0 : (ODD ? s_ns[row_shift(c, r)] : HALF);  // uniform
+#pragma unroll
+                        for (int g = 0; g < NGC; ++g) {
+                            uint4 w = make_uint4(kAlways, kAlways, kAlways, kAlways);
+                            if (4 * g < nreal) {
+                                w = philox4x32_10(make_uint4((uint32_t)(4 * r + g), t, ss.rid, c3), key);
+                                const bool ok = active;
+                                w.x = (ok && 4 * g + 0 < nreal) ? min(w.x, kAlways - 1u) : kAlways;
+                                w.y = (ok && 4 * g + 1 < nreal) ? min(w.y, kAlways - 1u) : kAlways;
+                                w.z = (ok && 4 * g + 2 < nreal) ? min(w.z, kAlways - 1u) : kAlways;
+                                w.w = (ok && 4 * g + 3 < nreal) ? min(w.w, kAlways - 1u) : kAlways;
+                            }
+                            buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
+                        }
                     }
                 }
                 return;
@@ -260,9 +276,11 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             // classes of row h (nibble 2j of s: the j-th colour site), stored as table offsets
             // n * NSB, 16 bits per attempt, the row's offsets from word h * OW
 #pragma unroll
-            for (int h = h0; h < h1; ++h) {
+            for (int hi = 0; hi < RH; ++hi) {
+            const int h = h0 + hi;
+            if ((RPR & 1) && h >= h1) break;
             const int r = r0 + h;
-            if (r >= NR) {  // padding row: class dim in every slot (no move)
+            if (PADROWS && r >= NR) {  // padding row: class dim in every slot (no move)
 #pragma unroll
                 for (int q = 0; q < G::OW; ++q) {
                     const int wd = h * G::OW + q;
@@ -484,7 +502,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
 #pragma unroll
             for (int h = 0; h < RPR; ++h) {
                 const int r = r0 + h;
-                if (r < NR) {  // padding rows have no spins
+                if (!PADROWS || r < NR) {  // padding rows have no spins
                     if constexpr (ODD) Rs[r * W + ln] ^= flipped[h];
                     else Rs[r * W + ln] ^= flipped[h] << (4 * row_shift(c, r));
                 }
@@ -504,7 +522,10 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     }
 }
 
-template <int DIM>
+// Kernels for the even sizes, the odd sizes and both: a context of one parity gets a kernel whose
+// register allocation is that of its own sizes (the odd sizes' larger records need more); a
+// context holding both gets one launch for all its tiles.  MODE 0 even, 1 odd, 2 both.
+template <int DIM, int MODE>
 __global__ void __launch_bounds__(kCkThreads, 1)
 muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ slots, uint32_t *__restrict__ spins,
                     const uint32_t *__restrict__ bonds, const uint32_t *__restrict__ thr,
@@ -512,29 +533,58 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
                     unsigned *__restrict__ diag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileDesc td = tiles[blockIdx.x];
+    const bool odd = (td.L & 1) != 0;
+    if ((MODE == 0 && odd) || (MODE == 1 && !odd)) return;  // the whole CTA, before any barrier
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CK(LL, WW) checker_tile<DIM, LL, WW>(td, blockIdx.x, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
     if (td.width == 16) {
         if constexpr (DIM == 3) {
-            if (td.L == 7) EAMC_CK(7, 16);
-            else if (td.L == 8) EAMC_CK(8, 16);
+            if constexpr (MODE != 0) {
+                if (td.L == 7) EAMC_CK(7, 16);
+            }
+            if constexpr (MODE != 1) {
+                if (td.L == 8) EAMC_CK(8, 16);
+            }
         }
         return;
     }
-    switch (td.L) {
-        case 3: EAMC_CK(3, 32); break;
-        case 4: EAMC_CK(4, 32); break;
-        case 5: EAMC_CK(5, 32); break;
-        case 6: EAMC_CK(6, 32); break;
-        case 7: EAMC_CK(7, 32); break;
-        case 8: EAMC_CK(8, 32); break;
-        case 9: EAMC_CK(9, 32); break;
-        case 10: EAMC_CK(10, 32); break;
-        case 11: EAMC_CK(11, 32); break;
-        case 12: EAMC_CK(12, 32); break;
-        default: break;
+    if constexpr (MODE != 0) {
+        switch (td.L) {
+            case 3: EAMC_CK(3, 32); break;
+            case 5: EAMC_CK(5, 32); break;
+            case 7: EAMC_CK(7, 32); break;
+            case 9: EAMC_CK(9, 32); break;
+            case 11: EAMC_CK(11, 32); break;
+            default: break;
+        }
+    }
+    if constexpr (MODE != 1) {
+        switch (td.L) {
+            case 4: EAMC_CK(4, 32); break;
+            case 6: EAMC_CK(6, 32); break;
+            case 8: EAMC_CK(8, 32); break;
+            case 10: EAMC_CK(10, 32); break;
+            case 12: EAMC_CK(12, 32); break;
+            default: break;
+        }
     }
 #undef EAMC_CK
+}
+
+template <int DIM, int MODE>
+cudaError_t ck_launch(int n_tiles, size_t smem, cudaStream_t st, const TileDesc *d_tiles, SlotState *d_slots,
+                      uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist,
+                      uint64_t n_sweeps, PhiloxKey key, int count_rt, unsigned *d_diag) {
+    static size_t set_limit = 0;
+    if (smem > set_limit) {
+        const cudaError_t e = cudaFuncSetAttribute(muca_checker_kernel<DIM, MODE>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_limit = smem;
+    }
+    muca_checker_kernel<DIM, MODE><<<n_tiles, kCkThreads, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr,
+                                                                       d_hist, n_sweeps, key, count_rt, d_diag);
+    return cudaGetLastError();
 }
 
 template <int DIM, int W>
@@ -569,23 +619,13 @@ size_t checker_smem_bytes(int dim, int L, int width) {
 cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,
                                   uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr,
                                   uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
-                                  unsigned *d_diag, cudaStream_t st) {
-    if (n_tiles <= 0 || n_sweeps == 0) return cudaSuccess;
-    static size_t set_limit[4] = {0, 0, 0, 0};
-    if (smem > set_limit[dim]) {
-        const cudaError_t e =
-            dim == 3 ? cudaFuncSetAttribute(muca_checker_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                     : cudaFuncSetAttribute(muca_checker_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        set_limit[dim] = smem;
-    }
-    if (dim == 3)
-        muca_checker_kernel<3><<<n_tiles, kCkThreads, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr, d_hist,
-                                                                 n_sweeps, key, count_rt, d_diag);
-    else
-        muca_checker_kernel<2><<<n_tiles, kCkThreads, smem, st>>>(d_tiles, d_slots, d_spins, d_bonds, d_thr, d_hist,
-                                                                 n_sweeps, key, count_rt, d_diag);
-    return cudaGetLastError();
+                                  unsigned *d_diag, cudaStream_t st, int parities) {
+    if (n_tiles <= 0 || n_sweeps == 0 || parities == 0) return cudaSuccess;
+    const int mode = parities == 1 ? 0 : (parities == 2 ? 1 : 2);
+#define EAMC_CKL(D, M) ck_launch<D, M>(n_tiles, smem, st, d_tiles, d_slots, d_spins, d_bonds, d_thr, d_hist, n_sweeps, key, count_rt, d_diag)
+    if (dim == 3) return mode == 0 ? EAMC_CKL(3, 0) : (mode == 1 ? EAMC_CKL(3, 1) : EAMC_CKL(3, 2));
+    return mode == 0 ? EAMC_CKL(2, 0) : (mode == 1 ? EAMC_CKL(2, 1) : EAMC_CKL(2, 2));
+#undef EAMC_CKL
 }
 
 }  // namespace eamc
