@@ -57,10 +57,10 @@ LATENCY_FLOOR_CYCLES = 35.4
 PT_ALG_OPS = 4.7
 # dram__bytes_read.sum + dram__bytes_write.sum of one production launch of the headline workload
 # (L=8, 1024 chains in tiles of 16, checkerboard kernel), ncu capture of this kernel version:
-# 13.73 MB + 0 B for a 2000-sweep launch.  It is the one-time staging of the threshold tables and
+# 13.69 MB + 0 B for a 2000-sweep launch.  It is the one-time staging of the threshold tables and
 # lattices, so it does not grow with the sweeps of a launch: a 10^4-sweep launch moves the same
 # bytes.
-SWEEP_TRAFFIC_BYTES = 13.73e6
+SWEEP_TRAFFIC_BYTES = 13.69e6
 
 
 def parse():
@@ -1115,7 +1115,7 @@ def main():
                      "frac": r["achieved_ops"] / r["alu_peak"], "traffic": SWEEP_TRAFFIC_BYTES,
                      "traffic_basis": "ncu dram read+write of one launch (one-time table and lattice "
                                       "staging, independent of the sweeps per launch)",
-                     "kernel": "muca_checker_kernel<3>" if W.order == "colour" else "muca_sweep_kernel<3>",
+                     "kernel": "muca_checker_kernel<3, 0>" if W.order == "colour" else "muca_sweep_kernel<3>",
                      "ops_per_attempt": ALG_OPS_PER_ATTEMPT,
                      "peak_basis": f"{r['sm_count']} SMs x 128 lane-instructions/clk x max SM clock "
                                    f"(MEASURED_PEAKS.json sm_max_mhz)"},
