@@ -237,7 +237,7 @@ def build_context(eamc, rank: int, stream_ptr: int, W=HEADLINE, ensembles=None, 
     if tuned:
         best = autotune.tune([(W.dim, W.L, n)] * len(ens_list), order=order_code(W.order))
     else:
-        best = {"widths": {str(W.L): eamc.narrow_width(W.dim, W.L)}, "persistent": False,
+        best = {"widths": {str(W.L): eamc.narrow_width(W.dim, W.L, order_code(W.order))}, "persistent": False,
                 "blocks_per_sm": 0, "sweeps_per_launch": 0}
     ctx = eamc.Context(seed=W.seed, device=0, stream=stream_ptr)
     ctx.set_sweep_order(order_code(W.order))
@@ -854,7 +854,7 @@ def bench_table_one_l8(n_real: int = 1024, prod_sweeps: int = 300_000, order: in
     t0 = time.perf_counter()
     res = scan.profile_scan(3, W.L, n_real, (W.alpha,), (W.pole,), seed=W.seed, dos_iters=W.iter_steps,
                             dos_sweeps=W.iter_sweeps, prod_sweeps=prod_sweeps, recursion=eamc.EA_REC_BERG,
-                            stream=stream.cuda_stream, tile_width=eamc.narrow_width(3, W.L),
+                            stream=stream.cuda_stream, tile_width=eamc.narrow_width(3, W.L, order),
                             order=order)
     wall = time.perf_counter() - t0
     pt_tau, pt_below = scan.pt_round_trips(3, W.L, n_real, PT_REPLICAS[W.L], res.e_g, seed=W.seed,

@@ -168,7 +168,9 @@ int muca_set_launch(ea_ctx *ctx, int persistent, uint64_t sweeps_per_launch, int
 int muca_set_sweep_order(ea_ctx *ctx, int order, int chains_per_cta);
 
 /* a8 -- chains per tile for chains of linear size L added afterwards (ea_init_disorder):
- * width 32 (the default, every L) or 16 (3D, L = 7, 8).  A tile is one
+ * width 32 (the default, every L), 16 (3D, L = 7, 8), or, for chains swept in the colour order
+ * only, 8 (3D, L = 9, 10) and 4 (3D, L = 11, 12); muca_run_sweeps in the lexicographic order
+ * refuses tiles of those two widths (EA_EINVAL).  A tile is one
  * warp; with width W < 32 each of its W chains runs on 32/W lanes side by side, so the tile needs
  * W/32 of the shared memory of a full one and these sizes keep their acceptance thresholds in
  * shared memory instead of reading them through L1: each chain runs faster, the SM holds fewer
@@ -180,6 +182,8 @@ int muca_set_tile_width(ea_ctx *ctx, int L, int width);
  * (*smem_bytes, may be NULL) and whether the thresholds live in shared memory
  * (*thresholds_in_smem, may be NULL).  EA_EINVAL for a width not available at this L. */
 int muca_get_tile_width(int dim, int L, int width, size_t *smem_bytes, int *thresholds_in_smem);
+/* The same for the colour-order kernel (muca_set_sweep_order). */
+int muca_get_tile_width_colour(int dim, int L, int width, size_t *smem_bytes, int *thresholds_in_smem);
 
 /* a8 / a9 -- every tile of linear size L runs multiplier x the requested sweeps in each
  * muca_run_sweeps call (default 1), so a launch over tiles of uneven L can give small lattices

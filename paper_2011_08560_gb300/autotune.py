@@ -1,8 +1,9 @@
 """Self-written autotuner for the batched MUCA sweep launch (a8).
 
 Knobs:
-  * chains per tile for each lattice size (muca_set_tile_width): 32, or 16 where the narrow tile
-    brings the acceptance thresholds into shared memory (L = 7, 8).  A narrow tile runs each of
+  * chains per tile for each lattice size (muca_set_tile_width): 32, or the narrow width that
+    brings the acceptance thresholds into shared memory (16 at L = 7, 8; in the colour order also
+    8 at L = 9, 10 and 4 at L = 11, 12).  A narrow tile runs each of
     its chains faster but holds half as many, so it wins when the batch is smaller than what the
     GPU can hold and loses when tiles queue for SMs;
   * the persistent work-queue grid vs one block per tile, and the resident blocks per SM of the
@@ -44,13 +45,13 @@ def signature(groups) -> str:
     return ";".join(f"{d}x{L}x{n}" for d, L, n in groups)
 
 
-def width_options(groups):
+def width_options(groups, order: int = 0):
     """Tile-width assignments to try: every L at 32, and each L that has a narrow width either
     way (all combinations; at most a few sizes have one)."""
-    narrow = sorted({(d, L) for d, L, _ in groups if eamc.narrow_width(d, L) != 32})
+    narrow = sorted({(d, L) for d, L, _ in groups if eamc.narrow_width(d, L, order) != 32})
     out = []
     for pick in itertools.product((False, True), repeat=len(narrow)):
-        out.append({str(L): (eamc.narrow_width(d, L) if p else 32) for (d, L), p in zip(narrow, pick)})
+        out.append({str(L): (eamc.narrow_width(d, L, order) if p else 32) for (d, L), p in zip(narrow, pick)})
     return out
 
 
@@ -80,7 +81,7 @@ def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, dev
         return db[key]["best"]
     stream = torch.cuda.Stream(device=device)
     results = []
-    for widths in width_options(groups):
+    for widths in width_options(groups, order):
         ctx = eamc.Context(seed=0x5EED, device=device, stream=stream.cuda_stream)
         ctx.set_sweep_order(order)
         for L, w in widths.items():

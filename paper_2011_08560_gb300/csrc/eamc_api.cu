@@ -356,10 +356,15 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     ctx_drop_graph(ctx);  // the arenas may move and the tile set changes
     int smem_optin = 0;
     EA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    const int W = sweep_width_supported(dim, L, ctx->tile_width[L]) ? ctx->tile_width[L] : kTile;
-    if (sweep_smem_bytes(dim, L, W) > (size_t)smem_optin)
-        return fail(EA_EINVAL, "L=%d needs %zu bytes of shared memory per block, the device allows %d", L,
-                    sweep_smem_bytes(dim, L, W), smem_optin);
+    // the tile width: the configured one where either sweep kernel has it (8 and 4 only the
+    // colour-order kernel), else 32
+    const int Wc = ctx->tile_width[L];
+    const bool lex_w = sweep_width_supported(dim, L, Wc), col_w = checker_smem_bytes(dim, L, Wc) > 0;
+    const int W = (lex_w || col_w) ? Wc : kTile;
+    const size_t need = std::max(lex_w || W == kTile ? sweep_smem_bytes(dim, L, W) : 0, checker_smem_bytes(dim, L, W));
+    if (need > (size_t)smem_optin)
+        return fail(EA_EINVAL, "L=%d needs %zu bytes of shared memory per block, the device allows %d", L, need,
+                    smem_optin);
     const int V = volume_of(dim, L), B = rows_of(dim, L);
     const int new_tiles = (n + W - 1) / W;
     const int tile0 = (int)ctx->tiles.size();
@@ -442,7 +447,7 @@ extern "C" int ea_init_disorder(ea_ctx *ctx, int dim, int L, int n, uint32_t rid
     ctx->bond_used = bond_used;
     ctx->w_used = w_used;
     ctx->max_V = std::max(ctx->max_V, V);
-    ctx->sweep_smem = std::max(ctx->sweep_smem, sweep_smem_bytes(dim, L, W));
+    if (sweep_width_supported(dim, L, W)) ctx->sweep_smem = std::max(ctx->sweep_smem, sweep_smem_bytes(dim, L, W));
     for (int k = 0; k < n; ++k) {
         const int slot = (tile0 + k / W) * kTile + k % W;
         ctx->chain_slot.push_back(slot);
@@ -665,6 +670,9 @@ int ctx_enqueue_sweeps(ea_ctx *ctx, uint64_t n_sweeps, int count_roundtrips) {
         }
         return EA_OK;
     }
+    for (const TileDesc &td : ctx->tiles)
+        if (!sweep_width_supported(td.dim, td.L, td.width))
+            return fail(EA_EINVAL, "tiles of %d chains at L=%d run only in the colour order", td.width, td.L);
     for (uint64_t done = 0; done < n_sweeps; done += chunk) {
         const uint64_t now = std::min(chunk, n_sweeps - done);
         if (ctx->persistent) {
@@ -726,9 +734,9 @@ extern "C" int muca_set_tile_width(ea_ctx *ctx, int L, int width) {
     if (!ctx) return fail(EA_EINVAL, "null context");
     if (L < 3 || L > 12) return fail(EA_EINVAL, "L must be in [3, 12] (got %d)", L);
     const int dim = ctx->dim ? ctx->dim : 3;
-    if (!sweep_width_supported(dim, L, width))
-        return fail(EA_EINVAL, "tile width %d is not available for dim=%d, L=%d (32 always; 16 for L=7,8 "
-                               "in 3D)", width, dim, L);
+    if (!sweep_width_supported(dim, L, width) && checker_smem_bytes(dim, L, width) == 0)
+        return fail(EA_EINVAL, "tile width %d is not available for dim=%d, L=%d (32 always; in 3D 16 for "
+                               "L=7,8, and in the colour order 8 for L=9,10 and 4 for L=11,12)", width, dim, L);
     ctx->tile_width[L] = width;
     return EA_OK;
 }
@@ -737,6 +745,14 @@ extern "C" int muca_get_tile_width(int dim, int L, int width, size_t *smem_bytes
     if (!sweep_width_supported(dim, L, width)) return fail(EA_EINVAL, "tile width %d unavailable", width);
     if (smem_bytes) *smem_bytes = sweep_smem_bytes(dim, L, width);
     if (thresholds_in_smem) *thresholds_in_smem = sweep_thresholds_in_smem(dim, L, width) ? 1 : 0;
+    return EA_OK;
+}
+
+extern "C" int muca_get_tile_width_colour(int dim, int L, int width, size_t *smem_bytes, int *thresholds_in_smem) {
+    const size_t b = checker_smem_bytes(dim, L, width);
+    if (b == 0) return fail(EA_EINVAL, "tile width %d unavailable in the colour order", width);
+    if (smem_bytes) *smem_bytes = b;
+    if (thresholds_in_smem) *thresholds_in_smem = checker_thresholds_in_smem(dim, L, width) ? 1 : 0;
     return EA_OK;
 }
 

@@ -106,8 +106,10 @@ cudaError_t launch_sweeps(const TileDesc *d_tiles, const int32_t *d_tile_list, i
                           const uint32_t *d_bonds, const uint32_t *d_thr, uint32_t *d_hist, uint64_t n_sweeps,
                           PhiloxKey key, int count_rt, unsigned *d_diag, cudaStream_t st);
 int sweep_blocks_per_sm(int dim, size_t smem);
-// the colour-order sweep (muca_checker.cu): one lane per chain, every L
+// the colour-order sweep (muca_checker.cu): one lane per chain, every L; widths 32 and (3D) 16 at
+// L = 7, 8, 8 at L = 9, 10, 4 at L = 11, 12 (0 bytes: not available)
 size_t checker_smem_bytes(int dim, int L, int width);
+bool checker_thresholds_in_smem(int dim, int L, int width);
 cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,
                                   uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr,
                                   uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,

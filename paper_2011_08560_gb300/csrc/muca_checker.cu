@@ -84,7 +84,7 @@ __host__ __device__ constexpr int ck_sites_max(int L) {  // most colour-c sites 
 
 template <int DIM, int L, int W>
 struct CkGeo {
-    static_assert(W == 32 || W == 16, "tile width");
+    static_assert(W == 32 || W == 16 || W == 8 || W == 4, "tile width");
     using T = CkRow<L>;
     static constexpr int NCOL = (L & 1) ? 3 : 2;    // colour passes per sweep
     static constexpr int NR = DIM == 3 ? L * L : L;  // rows along x
@@ -537,13 +537,19 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
     if ((MODE == 0 && odd) || (MODE == 1 && !odd)) return;  // the whole CTA, before any barrier
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CK(LL, WW) checker_tile<DIM, LL, WW>(td, blockIdx.x, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
-    if (td.width == 16) {
+    // narrow tiles (3D): 16 chains at L = 7, 8, 8 at L = 9, 10, 4 at L = 11, 12, each chain on
+    // 32 / width lanes, so that the thresholds fit in shared memory
+    if (td.width != 32) {
         if constexpr (DIM == 3) {
             if constexpr (MODE != 0) {
-                if (td.L == 7) EAMC_CK(7, 16);
+                if (td.width == 16 && td.L == 7) EAMC_CK(7, 16);
+                else if (td.width == 8 && td.L == 9) EAMC_CK(9, 8);
+                else if (td.width == 4 && td.L == 11) EAMC_CK(11, 4);
             }
             if constexpr (MODE != 1) {
-                if (td.L == 8) EAMC_CK(8, 16);
+                if (td.width == 16 && td.L == 8) EAMC_CK(8, 16);
+                else if (td.width == 8 && td.L == 10) EAMC_CK(10, 8);
+                else if (td.width == 4 && td.L == 12) EAMC_CK(12, 4);
             }
         }
         return;
@@ -608,12 +614,27 @@ size_t checker_smem_w(int L) {
 
 size_t checker_smem_bytes(int dim, int L, int width) {
     if (L < 3 || L > 12) return 0;
-    if (width == 16) {
+    if (width != 32) {
         if (dim != 3) return 0;
-        return L == 7 ? CkGeo<3, 7, 16>::SMEM : (L == 8 ? CkGeo<3, 8, 16>::SMEM : 0);
+        if (width == 16) return L == 7 ? CkGeo<3, 7, 16>::SMEM : (L == 8 ? CkGeo<3, 8, 16>::SMEM : 0);
+        if (width == 8) return L == 9 ? CkGeo<3, 9, 8>::SMEM : (L == 10 ? CkGeo<3, 10, 8>::SMEM : 0);
+        if (width == 4) return L == 11 ? CkGeo<3, 11, 4>::SMEM : (L == 12 ? CkGeo<3, 12, 4>::SMEM : 0);
+        return 0;
     }
     if (width != 32) return 0;
     return dim == 3 ? checker_smem_w<3, 32>(L) : checker_smem_w<2, 32>(L);
+}
+
+bool checker_thresholds_in_smem(int dim, int L, int width) {
+    if (checker_smem_bytes(dim, L, width) == 0) return false;
+#define EAMC_TS(D, LL, WW) if (dim == D && L == LL && width == WW) return CkGeo<D, LL, WW>::SMEM_THR;
+    EAMC_TS(3, 7, 16) EAMC_TS(3, 8, 16) EAMC_TS(3, 9, 8) EAMC_TS(3, 10, 8) EAMC_TS(3, 11, 4) EAMC_TS(3, 12, 4)
+    EAMC_TS(3, 3, 32) EAMC_TS(3, 4, 32) EAMC_TS(3, 5, 32) EAMC_TS(3, 6, 32) EAMC_TS(3, 7, 32) EAMC_TS(3, 8, 32)
+    EAMC_TS(3, 9, 32) EAMC_TS(3, 10, 32) EAMC_TS(3, 11, 32) EAMC_TS(3, 12, 32)
+    EAMC_TS(2, 3, 32) EAMC_TS(2, 4, 32) EAMC_TS(2, 5, 32) EAMC_TS(2, 6, 32) EAMC_TS(2, 7, 32) EAMC_TS(2, 8, 32)
+    EAMC_TS(2, 9, 32) EAMC_TS(2, 10, 32) EAMC_TS(2, 11, 32) EAMC_TS(2, 12, 32)
+#undef EAMC_TS
+    return false;
 }
 
 cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,

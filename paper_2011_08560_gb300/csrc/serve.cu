@@ -369,6 +369,13 @@ extern "C" int ea_srv_create(ea_srv **out, int device, void *cuda_stream, uint64
     int rc = ea_create(&s->ctx, device, cuda_stream, seed);
     if (rc) { delete s; return rc; }
     if ((rc = muca_set_sweep_order(s->ctx, cfg->sweep_order, 0))) { ea_destroy(s->ctx); delete s; return rc; }
+    if (cfg->sweep_order == EA_ORDER_COLOUR) {
+        // the narrowest tiles whose thresholds fit in shared memory: each served chain runs as
+        // fast as it can (jobs are few per lattice size), the pool holds fewer lanes per tile
+        for (int L : s->Ls)
+            for (int w : {4, 8, 16})
+                if (muca_set_tile_width(s->ctx, L, w) == EA_OK) break;
+    }
     bool ok = cudaMalloc(&s->d_ring, kRingCap * sizeof(SrvRecord)) == cudaSuccess &&
               cudaMalloc(&s->d_head, sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&s->d_attempts, sizeof(unsigned long long)) == cudaSuccess &&

@@ -120,6 +120,7 @@ SIGNATURES = {
     "muca_set_tile_width": (_i, [P, _i, _i]),
     "muca_set_sweep_order": (_i, [P, _i, _i]),
     "muca_get_tile_width": (_i, [_i, _i, _i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i)]),
+    "muca_get_tile_width_colour": (_i, [_i, _i, _i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i)]),
     "muca_update_weights_subset": (_i, [P, P, _i]),
     "muca_copy_weights": (_i, [P, P, P, _i]),
     "ea_graph_capture": (_i, [P, _i, _u64, _i, _i]),
@@ -164,19 +165,21 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
-def tile_width_info(dim: int, L: int, width: int):
+def tile_width_info(dim: int, L: int, width: int, order: int = 0):
     """(dynamic shared memory per sweep block, thresholds in shared memory?) for tiles of this
-    (dim, L, width), or None when that width is not available."""
+    (dim, L, width) in sweep order `order`, or None when that width is not available."""
     smem, in_smem = ctypes.c_size_t(0), ctypes.c_int(0)
-    if lib().muca_get_tile_width(dim, L, width, ctypes.byref(smem), ctypes.byref(in_smem)) != EA_OK:
+    fn = lib().muca_get_tile_width_colour if order == 1 else lib().muca_get_tile_width
+    if fn(dim, L, width, ctypes.byref(smem), ctypes.byref(in_smem)) != EA_OK:
         return None
     return smem.value, bool(in_smem.value)
 
 
-def narrow_width(dim: int, L: int) -> int:
-    """The narrowest tile width available at (dim, L) (32 when there is no narrow one)."""
-    for w in (16,):
-        if tile_width_info(dim, L, w):
+def narrow_width(dim: int, L: int, order: int = 0) -> int:
+    """The narrowest tile width available at (dim, L) in sweep order `order` (32 when there is
+    no narrow one)."""
+    for w in (4, 8, 16):
+        if tile_width_info(dim, L, w, order):
             return w
     return 32
 

@@ -204,3 +204,33 @@ def test_colour_snapshot_resume_and_narrow_tiles(eamc, orc):
     for k, c in enumerate(chains):
         assert np.array_equal(S2[k, :c.V], c.S) and E2[k] == c.E
     resumed.check()
+
+
+@pytest.mark.parametrize("L,width,n", [(9, 8, 13), (10, 8, 9), (11, 4, 6), (12, 4, 5)])
+def test_narrow_colour_tiles_bit_exact(eamc, orc, L, width, n):
+    """Tiles of 8 (L = 9, 10) and 4 chains (L = 11, 12), each chain on 32 / width lanes with its
+    thresholds in shared memory: the colour order's trajectories, a partly filled last tile."""
+    info = eamc.tile_width_info(3, L, width, order=1)
+    assert info is not None and info[1], info           # thresholds in shared memory
+    assert eamc.tile_width_info(3, L, width, order=0) is None
+    rng = np.random.default_rng(L * 7 + width)
+    ctx = eamc.Context(seed=SEED)
+    ctx.set_sweep_order(eamc.EA_ORDER_COLOUR)
+    ctx.set_tile_width(L, width)
+    ctx.init_disorder(3, L, n, rid0=21, stream=1)
+    chains = _chains(orc, 3, L, n, 21, 1)
+    thr = [orc.quantize(3, _random_lnw(rng, c.b_top, 0.4)) for c in chains]
+    ctx.set_thresholds(0, _pad(thr))
+    eg = np.array([c.E - 8 for c in chains], dtype=np.int32)
+    ctx.set_eg(0, n, eg)
+    for c, e in zip(chains, eg):
+        c.rt.e_g = int(e)
+    ctx.run_sweeps(6, count_roundtrips=True)
+    for c, th in zip(chains, thr):
+        c.sweeps(6, th, count_rt=True)
+    _compare(ctx, chains)
+    ctx.check()
+    # the lexicographic kernel has no tiles of this width
+    ctx.set_sweep_order(eamc.EA_ORDER_LEX)
+    with pytest.raises(eamc.EamcError):
+        ctx.run_sweeps(1)
