@@ -13,13 +13,13 @@
 // loads, two selects and a compare per attempt on the consumer warp (the lexicographic order
 // has to carry two candidate classes as well, because consecutive sites are neighbours).
 //
-// Eight warps; warp w issues on scheduler w % 4, and each scheduler has one busy role: 0 the
-// consumer; 1 and 5 the classes of the first and second half of a record's rows; 3 and 7 their
-// random words; 2 the measurement (lowest energy, round trips, histogram), one record behind the
-// consumer; 4 and 6 only take part in the barriers.  A record is RPR consecutive rows of one pass
-// (four where the row count allows it and L <= 8, else two): the colour-c sites of
-// those rows, RPR L / 2 attempts, with each attempt's class as its table offset n * NSB (16
-// bits) and its random word.  The consumer leaves the bin after every attempt for the
+// Eight warps; warp w issues on scheduler w % 4: 0 the consumer, alone on its scheduler; 1 and 5
+// the classes of a record's rows; 3 and 6 their random words (the Philox calls are the heaviest
+// producer work, so they sit on two schedulers; a narrow tile deals the rows to the lane groups
+// of these warps as well); 2 the measurement (lowest energy, round trips, histogram), one record
+// behind the consumer; 4 and 7 only take part in the barriers.  A record is RPR consecutive rows
+// of one pass (two to eight, by size): the colour-c sites of those rows, RPR L / 2 attempts for
+// even L, with each attempt's class as its table offset n * NSB (16 bits) and its random word.  The consumer leaves the bin after every attempt for the
 // measurement.  Within a pass the producers may run any number of records ahead (the classes
 // read only the other colour's spins and each site's own spin, which its own record changes), so
 // they run LAG records ahead; at the start of a pass one extra barrier lets them refill, because
@@ -46,15 +46,15 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr int kCkWarps = 8;
 constexpr int kCkMeasure = 2;
 constexpr int kCkThreads = 32 * kCkWarps;
-// warp roles: classes of row h of a record (warps 1, 5), random words of row h (warps 3, 7)
+// warp roles: classes of a record's rows (warps 1, 5), their random words (warps 3, 6)
 __device__ __forceinline__ bool ck_classes(int warp) { return warp == 1 || warp == 5; }
-__device__ __forceinline__ bool ck_random(int warp) { return warp == 3 || warp == 7; }
+__device__ __forceinline__ bool ck_random(int warp) { return warp == 3 || warp == 6; }
 
 template <int L>
 using CkRow = typename std::conditional<(L <= 8), uint32_t, uint64_t>::type;
 
 template <class T, int L>
-__device__ __forceinline__ T ck_mask() {
+__device__ __forceinline__ constexpr T ck_mask() {
     return (4 * L == 8 * (int)sizeof(T)) ? ~T(0) : ((T(1) << (4 * L)) - 1);
 }
 
@@ -95,11 +95,14 @@ struct CkGeo {
     static constexpr int HALF = (L & 1) ? ck_sites_max(L) : L / 2;
     static_assert(HALF <= 4 || (L & 1) == 0, "one Philox call per row and pass for odd L");
     static constexpr int NGC = (HALF + 3) / 4;      // Philox calls per row and pass
-    // rows per record: even L four where the rows divide into fours, up to L = 8, else two; odd
-    // L a plane's L rows (the whole lattice for 2D and L = 3) up to L = 9, else two, the last
-    // record of a pass padded with rows of padding slots
-    static constexpr int RPR = (L & 1) ? (L <= 9 ? (NR <= 9 ? NR : L) : 2) : ((NR % 4 == 0 && L <= 8) ? 4 : 2);
+    // rows per record (fewer, longer records spread the per-record cost of the barrier and the
+    // hand-over over more attempts; measured per size): 3D even L eight at L = 8, else four where
+    // the rows divide into fours, else two; odd L a plane's L rows (the whole lattice for 2D and
+    // L = 3) up to L = 9, else two, the last record of a pass padded with rows of padding slots
+    static constexpr int RPR = (L & 1) ? (L <= 9 ? (NR <= 9 ? NR : L) : 2)
+                                       : ((DIM == 3 && L == 8) ? 8 : ((NR % 4 == 0 && (L <= 8 || DIM == 3)) ? 4 : 2));
     static constexpr int NA = RPR * HALF;           // attempts per record
+    static_assert(NA <= 32, "the measurement keeps a record's attempts in 32-bit masks");
     static constexpr int NP = (NR + RPR - 1) / RPR;  // records per pass
     static constexpr int OW = (HALF + 1) / 2;       // 32-bit words of 16-bit class offsets per row
     static constexpr int OFFQ = (RPR * OW + 3) / 4; // uint4 slots of class offsets (row h at word h * OW)
@@ -109,7 +112,7 @@ struct CkGeo {
     // the consumer after barrier g (and preloaded after g-1) while record g+LAG is written; one
     // buffer more than that needs (measured faster)
     static constexpr int NBUF = LAG + 2;
-    static constexpr int FIELDS = DIM + 1;          // S, Jx, Jy, (Jz)
+    static constexpr int FIELDS = 2;                // S, and the bonds (Jx, Jy, Jz at bits 0, 1, 2 of a site's nibble)
     static constexpr size_t LATTICE_BYTES = (size_t)FIELDS * NR * W * sizeof(T);
     static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * W * 16;
     static constexpr size_t RES_BYTES = (size_t)2 * NA * W * sizeof(int);  // bin row offset after each attempt, two records
@@ -117,12 +120,25 @@ struct CkGeo {
     static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES;
     static constexpr bool SMEM_THR = BASE_BYTES + THR_BYTES <= 225 * 1024;
     static constexpr size_t SMEM = BASE_BYTES + (SMEM_THR ? THR_BYTES : 0);
+    // thresholds addressed by 32-bit shared addresses; measured with the same launches: L = 6 in
+    // tiles of 32 2.5 % faster, L = 10 in tiles of 8 1.5 % faster, L = 8 in tiles of 16 2.5 % slower
+    static constexpr bool SADDR = SMEM_THR && !(L == 8 && W == 16);
 };
 
-template <bool SMEM>
-__device__ __forceinline__ uint32_t ck_thr(const char *p) {
-    if constexpr (SMEM) return *reinterpret_cast<const uint32_t *>(p);
-    else return __ldg(reinterpret_cast<const uint32_t *>(p));
+// a threshold at byte offset a: in shared memory either at the 32-bit shared address a (SADDR: the
+// table base is already in a, so the selected address is the load's operand) or at tab + a; in
+// global memory at tab + a
+template <bool SMEM, bool SADDR>
+__device__ __forceinline__ uint32_t ck_thr(const char *tab, int a) {
+    if constexpr (SMEM && SADDR) {
+        uint32_t v;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+        return v;
+    } else if constexpr (SMEM) {
+        return *reinterpret_cast<const uint32_t *>(tab + a);
+    } else {
+        return __ldg(reinterpret_cast<const uint32_t *>(tab + a));
+    }
 }
 
 template <int DIM, int L, int W>
@@ -142,9 +158,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     const bool owner = lane < W;
 
     T *Rs = reinterpret_cast<T *>(smem_raw);  // spins, nibble x = 1 if S = -1
-    T *JXs = Rs + NR * W;                     // bond (x, x+1) has J = -1
-    T *JYs = Rs + 2 * NR * W;                 // bond (y, y+1)
-    T *JZs = Rs + 3 * NR * W;                 // bond (z, z+1)  (DIM == 3)
+    // bonds of a row, nibble x: bit 0 J(x, x+1) = -1, bit 1 J(y, y+1) = -1, bit 2 J(z, z+1) = -1
+    T *JBs = Rs + NR * W;
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
     int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2 records][NA][W]
     // odd L: for each colour shift s, the row's colour sites as a byte list (x positions, 0xFF
@@ -186,9 +201,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             if constexpr (DIM == 3) jz |= T((gbd[i * DIM + 2] >> ln) & 1u) << (4 * x);
         }
         Rs[row * W + ln] = r;
-        JXs[row * W + ln] = jx;
-        JYs[row * W + ln] = jy;
-        if constexpr (DIM == 3) JZs[row * W + ln] = jz;
+        JBs[row * W + ln] = jx | (jy << 1) | (jz << 2);
     }
 
     const int slot = tile * kTile + ln;
@@ -197,7 +210,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     const uint64_t lrow = td.w_base + (uint64_t)ln * G::B;
     // element (b, n) of this chain's table at byte offset b * RSB + n * NSB from `tab`; rows
     // -DIM .. B-1+DIM are addressable (zero padding), so a candidate row one move away from a
-    // valid row needs no clamp
+    // valid row needs no clamp.  Bin row offsets carry the base rb0: the table's 32-bit shared
+    // address when it is read by shared addresses (SADDR), else 0
     constexpr int NSB = G::SMEM_THR ? 4 * W : 4;
     constexpr int RSB = 8 * NSB;
     const char *tab;
@@ -222,6 +236,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     } else {
         tab = reinterpret_cast<const char *>(thr + lrow * 8);
     }
+    const int rb0 = G::SADDR ? (int)__cvta_generic_to_shared(tab) : 0;
     const uint64_t t0 = ss.t;
     const uint64_t n_pass = n_sweeps * NCOL;  // colour passes
 
@@ -233,16 +248,19 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
         auto produce = [&](int c, int p, uint32_t t, int k) {
             uint4 *buf = hand + k * G::HQ * W;
             const int r0 = RPR * p;
-            // this warp prepares rows h0 .. h1 - 1 of the record (the first warp of a role one more
-            // for odd RPR); loops of RH iterations with a guard keep the trip count a constant
-            constexpr int RH = (RPR + 1) / 2;
-            const int h0 = warp >= 4 ? RH : 0, h1 = warp >= 4 ? RPR : RH;
+            // a role's rows are dealt to its workers, the 32 / W lane groups of its two warps (a
+            // narrow tile's lanes above W would otherwise repeat lanes 0 .. W-1): worker wk takes
+            // rows wk, wk + NWK, ...; a loop of RH iterations with a guard keeps the trip count a
+            // constant
+            constexpr int NWK = 2 * (32 / W);
+            constexpr int RH = (RPR + NWK - 1) / NWK;
+            const int wk = (warp >= 4 ? 32 / W : 0) + lane / W;
             if (ck_random(warp)) {  // clamped as in the lexicographic kernel; padding: never accepts
                 const uint32_t c3 = (uint32_t)(5 + c) | (ss.stream << 8);
 #pragma unroll
                 for (int hi = 0; hi < RH; ++hi) {
-                    const int h = h0 + hi;
-                    if ((RPR & 1) && h >= h1) break;
+                    const int h = wk + hi * NWK;
+                    if ((RPR % NWK) != 0 && h >= RPR) break;
                     const int r = r0 + h;
                     if constexpr (!ODD && !PADROWS) {  // every slot is a site
 #pragma unroll
@@ -255,7 +273,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                             buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
                         }
                     } else {
-                        const int nreal = r >= NR ? 0 : (ODD ? s_ns[row_shift(c, r)] : HALF);  // uniform
+                        const int nreal = r >= NR ? 0 : (ODD ? s_ns[row_shift(c, r)] : HALF);
 #pragma unroll
                         for (int g = 0; g < NGC; ++g) {
                             uint4 w = make_uint4(kAlways, kAlways, kAlways, kAlways);
@@ -277,8 +295,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             // n * NSB, 16 bits per attempt, the row's offsets from word h * OW
 #pragma unroll
             for (int hi = 0; hi < RH; ++hi) {
-            const int h = h0 + hi;
-            if ((RPR & 1) && h >= h1) break;
+            const int h = wk + hi * NWK;
+            if ((RPR % NWK) != 0 && h >= RPR) break;
             const int r = r0 + h;
             if (PADROWS && r >= NR) {  // padding row: class dim in every slot (no move)
 #pragma unroll
@@ -293,16 +311,17 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             uint32_t xs = 0u;  // odd L: the row's colour sites (bytes, 0xFF padding)
             {
                 const int y = r % L, z = DIM == 3 ? r / L : 0;
-                const T R = Rs[r * W + ln];
-                const T uxp = R ^ ck_next<T, L>(R) ^ JXs[r * W + ln];
+                constexpr T M1 = ck_mask<T, L>() & (T)0x1111111111111111ull;  // bit 0 of every nibble
+                const T R = Rs[r * W + ln], JB = JBs[r * W + ln];
+                const T uxp = R ^ ck_next<T, L>(R) ^ (JB & M1);
                 const int ryp = (y == L - 1) ? r - (L - 1) : r + 1;
                 const int rym = (y == 0) ? r + (L - 1) : r - 1;
-                T sum = uxp + ck_prev<T, L>(uxp) + (R ^ Rs[ryp * W + ln] ^ JYs[r * W + ln]) +
-                        (R ^ Rs[rym * W + ln] ^ JYs[rym * W + ln]);
+                T sum = uxp + ck_prev<T, L>(uxp) + (R ^ Rs[ryp * W + ln] ^ ((JB >> 1) & M1)) +
+                        (R ^ Rs[rym * W + ln] ^ ((JBs[rym * W + ln] >> 1) & M1));
                 if constexpr (DIM == 3) {
                     const int rzp = (z == L - 1) ? r - (L - 1) * L : r + L;
                     const int rzm = (z == 0) ? r + (L - 1) * L : r - L;
-                    sum += (R ^ Rs[rzp * W + ln] ^ JZs[r * W + ln]) + (R ^ Rs[rzm * W + ln] ^ JZs[rzm * W + ln]);
+                    sum += (R ^ Rs[rzp * W + ln] ^ ((JB >> 2) & M1)) + (R ^ Rs[rzm * W + ln] ^ ((JBs[rzm * W + ln] >> 2) & M1));
                 }
                 if constexpr (ODD) {
                     s = sum;
@@ -336,8 +355,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
         // ---- measurement, one record behind the consumer
         int phase = ss.phase, nrt = ss.n_rt;
         int64_t tf = ss.t_first, tl = ss.t_last;
-        const int topB = ss.b_top * RSB, botB = ss.b_g * RSB;
-        int pmin = ss.b_min * RSB, pnow = ss.b * RSB;
+        const int topB = rb0 + ss.b_top * RSB, botB = rb0 + ss.b_g * RSB;
+        int pmin = rb0 + ss.b_min * RSB, pnow = rb0 + ss.b * RSB;
         bool out_of_range = false;
         uint64_t mrec = 0;  // records measured
         auto measure = [&](uint64_t gm) {  // record gm: the bin row offset after each of its attempts
@@ -354,7 +373,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                 if (a == NA - 1) pnow = pr;
             }
             pmin = min(pmin, lo);
-            out_of_range |= (lo < 0) | (hi > topB);
+            out_of_range |= (lo < rb0) | (hi > topB);
             const uint64_t sweep = mrec / (NCOL * NP);
             if (count_rt && active && ((phase == 1) ? mbot : mtop) != 0u) {
                 const int64_t t = (int64_t)(t0 + sweep);
@@ -368,7 +387,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                     else { nrt += 1; tl = t; phase = 1; }
                 }
             }
-            if (++mrec % (NCOL * NP) == 0 && active && owner) atomicAdd(&hist[lrow + pnow / RSB], 1u);
+            if (++mrec % (NCOL * NP) == 0 && active && owner) atomicAdd(&hist[lrow + (pnow - rb0) / RSB], 1u);
         };
         uint64_t g = 0;  // records the consumer has been given
         for (uint64_t q = 0; q < n_pass; ++q) {
@@ -388,8 +407,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
         __syncthreads();
         if (warp == kCkMeasure) {
             if (g > 0) measure(g - 1);
-            ss.b = pnow / RSB;
-            ss.b_min = pmin / RSB;
+            ss.b = (pnow - rb0) / RSB;
+            ss.b_min = (pmin - rb0) / RSB;
             ss.phase = phase;
             ss.n_rt = nrt;
             ss.t_first = tf;
@@ -405,7 +424,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     // ---- consumer
     // the previous attempt, applied lazily: row offset it was evaluated at (rq), offset change if
     // it was accepted (dq) and whether it was (pa)
-    int rq = ss.b * RSB, dq = 0;
+    int rq = rb0 + ss.b * RSB, dq = 0;
     bool pa = false;
     uint32_t thA = 0u, thB = 0u;  // candidate thresholds of the next attempt (previous rejected / accepted)
     uint4 noff[G::OFFQ], nrr[RPR * NGC];  // the next record (read one barrier early)
@@ -437,18 +456,19 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             const int r0 = RPR * k;
             int on = (int)(off[0] & 0xFFFFu);  // this attempt's class offset
             if (!have_next) {
-                thA = ck_thr<G::SMEM_THR>(tab + rq + on);
-                thB = ck_thr<G::SMEM_THR>(tab + rq + dq + on);
+                thA = ck_thr<G::SMEM_THR, G::SADDR>(tab, rq + on);
+                thB = ck_thr<G::SMEM_THR, G::SADDR>(tab, rq + dq + on);
             }
             have_next = false;
             int *resb = res + (int)(g & 1) * NA * W + ln;
             // even L: bit 8j of flipped[h] is the row's j-th colour site (spread at the row's end);
             // odd L: the site's own nibble, at the shifts fsh of the row's colour sites
-            T flipped[RPR];
+            T flipped[RPR], rold[RPR];  // rold: the record's spin rows, read before its attempts
             uint32_t fsh[RPR];
 #pragma unroll
             for (int h = 0; h < RPR; ++h) {
                 flipped[h] = 0;
+                rold[h] = (!PADROWS || r0 + h < NR) ? Rs[(r0 + h) * W + ln] : T(0);
                 if constexpr (ODD) {  // padding bytes (0xFF) become x = 0: they never accept
                     const uint32_t xs = r0 + h < NR ? s_xs[row_shift(c, r0 + h)] : 0u;
                     fsh[h] = xs & ~(((xs >> 7) & 0x01010101u) * 0xFFu);
@@ -477,8 +497,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                 const int aA0 = rq + off1, aA1 = rB + off1, aB0 = aA0 + dx, aB1 = aA1 + dx;
                 uint32_t nA = 0u, nB = 0u;
                 if (next) {
-                    nA = ck_thr<G::SMEM_THR>(tab + (pa ? aA1 : aA0));
-                    nB = ck_thr<G::SMEM_THR>(tab + (pa ? aB1 : aB0));
+                    nA = ck_thr<G::SMEM_THR, G::SADDR>(tab, pa ? aA1 : aA0);
+                    nB = ck_thr<G::SMEM_THR, G::SADDR>(tab, pa ? aB1 : aB0);
                 }
                 const uint32_t th = pa ? thB : thA;
                 const int rx = pa ? rB : rq;
@@ -503,8 +523,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             for (int h = 0; h < RPR; ++h) {
                 const int r = r0 + h;
                 if (!PADROWS || r < NR) {  // padding rows have no spins
-                    if constexpr (ODD) Rs[r * W + ln] ^= flipped[h];
-                    else Rs[r * W + ln] ^= flipped[h] << (4 * row_shift(c, r));
+                    if constexpr (ODD) Rs[r * W + ln] = rold[h] ^ flipped[h];
+                    else Rs[r * W + ln] = rold[h] ^ (flipped[h] << (4 * row_shift(c, r)));
                 }
             }
         }
