@@ -96,11 +96,15 @@ struct CkGeo {
     static_assert(HALF <= 4 || (L & 1) == 0, "one Philox call per row and pass for odd L");
     static constexpr int NGC = (HALF + 3) / 4;      // Philox calls per row and pass
     // rows per record (fewer, longer records spread the per-record cost of the barrier and the
-    // hand-over over more attempts; measured per size): 3D even L eight at L = 8, else four where
-    // the rows divide into fours, else two; odd L a plane's L rows (the whole lattice for 2D and
-    // L = 3) up to L = 9, else two, the last record of a pass padded with rows of padding slots
+    // hand-over over more attempts; measured per size, longer records where they cost the other
+    // sizes of the same kernel nothing through its register allocation): 3D even L eight at
+    // L = 8, six at L = 6, else four where the rows divide into fours, else two; odd L a plane's L
+    // rows (the whole lattice for 2D and L = 3) up to L = 9, else two, the last record of a pass
+    // padded with rows of padding slots
     static constexpr int RPR = (L & 1) ? (L <= 9 ? (NR <= 9 ? NR : L) : 2)
-                                       : ((DIM == 3 && L == 8) ? 8 : ((NR % 4 == 0 && (L <= 8 || DIM == 3)) ? 4 : 2));
+                                       : (DIM == 3 && L == 8) ? 8
+                                       : (DIM == 3 && L == 6) ? 6
+                                       : ((NR % 4 == 0 && (L <= 8 || DIM == 3)) ? 4 : 2);
     static constexpr int NA = RPR * HALF;           // attempts per record
     static_assert(NA <= 32, "the measurement keeps a record's attempts in 32-bit masks");
     static constexpr int NP = (NR + RPR - 1) / RPR;  // records per pass
