@@ -1,7 +1,7 @@
 """The colour-order sweep kernels against the oracle's colour order, element by element: spins,
 energies, histograms and round-trip records bit-exact, weights to 1e-12.  One kernel, one lane
 per chain, for every L: even L two colour passes, odd L three with rows padded to the most
-colour sites of a row; records of two or four rows or a plane, one or two records of look-ahead,
+colour sites of a row; records of two to eight rows or a plane, one or two records of look-ahead,
 padded last records, 2D and 3D, full and narrow tiles; launch splitting, captured graphs,
 contexts holding both parities and the weight recursions (the chains-per-CTA argument has no
 effect)."""
