@@ -56,11 +56,11 @@ LATENCY_FLOOR_CYCLES = 35.4
 # 40 ops, 5 ops per plane) and the flip: about 150 lane-operations per 32 attempts
 PT_ALG_OPS = 4.7
 # dram__bytes_read.sum + dram__bytes_write.sum of one production launch of the headline workload
-# (L=8, 1024 chains in tiles of 16, checkerboard kernel), ncu capture of this kernel version:
-# 13.64 MB + 0 B for a 2000-sweep launch.  It is the one-time staging of the threshold tables and
+# (L=8, 1024 chains in tiles of 8, checkerboard kernel), ncu capture of this kernel version:
+# 14.21 MB + 0 B for a 2000-sweep launch.  It is the one-time staging of the threshold tables and
 # lattices, so it does not grow with the sweeps of a launch: a 10^4-sweep launch moves the same
 # bytes.
-SWEEP_TRAFFIC_BYTES = 13.64e6
+SWEEP_TRAFFIC_BYTES = 14.21e6
 
 
 def parse():

@@ -169,7 +169,7 @@ int muca_set_sweep_order(ea_ctx *ctx, int order, int chains_per_cta);
 
 /* a8 -- chains per tile for chains of linear size L added afterwards (ea_init_disorder):
  * width 32 (the default, every L), 16 (3D, L = 7, 8), or, for chains swept in the colour order
- * only, 8 (3D, L = 9, 10) and 4 (3D, L = 11, 12); muca_run_sweeps in the lexicographic order
+ * only, 8 (3D, L = 8, 9, 10) and 4 (3D, L = 11, 12); muca_run_sweeps in the lexicographic order
  * refuses tiles of those two widths (EA_EINVAL).  A tile is one
  * warp; with width W < 32 each of its W chains runs on 32/W lanes side by side, so the tile needs
  * W/32 of the shared memory of a full one and these sizes keep their acceptance thresholds in

@@ -46,12 +46,13 @@ def signature(groups) -> str:
 
 
 def width_options(groups, order: int = 0):
-    """Tile-width assignments to try: every L at 32, and each L that has a narrow width either
-    way (all combinations; at most a few sizes have one)."""
-    narrow = sorted({(d, L) for d, L, _ in groups if eamc.narrow_width(d, L, order) != 32})
+    """Tile-width assignments to try: every L at 32, and each L that has narrow widths at each of
+    them (all combinations; at most a few sizes have one, at most two)."""
+    narrow = sorted({(d, L) for d, L, _ in groups if eamc.narrow_widths(d, L, order)})
+    choices = [[32] + eamc.narrow_widths(d, L, order) for d, L in narrow]
     out = []
-    for pick in itertools.product((False, True), repeat=len(narrow)):
-        out.append({str(L): (eamc.narrow_width(d, L, order) if p else 32) for (d, L), p in zip(narrow, pick)})
+    for pick in itertools.product(*choices):
+        out.append({str(L): w for (d, L), w in zip(narrow, pick) if w != 32})
     return out
 
 

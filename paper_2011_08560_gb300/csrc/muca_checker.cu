@@ -561,8 +561,9 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
     if ((MODE == 0 && odd) || (MODE == 1 && !odd)) return;  // the whole CTA, before any barrier
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CK(LL, WW) checker_tile<DIM, LL, WW>(td, blockIdx.x, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
-    // narrow tiles (3D): 16 chains at L = 7, 8, 8 at L = 9, 10, 4 at L = 11, 12, each chain on
-    // 32 / width lanes, so that the thresholds fit in shared memory
+    // narrow tiles (3D): 16 chains at L = 7, 8, 8 at L = 8, 9, 10, 4 at L = 11, 12, each chain on
+    // 32 / width lanes, so that the thresholds fit in shared memory (at L = 8 tiles of 8 spread a
+    // batch over twice the SMs, each with half the producer work)
     if (td.width != 32) {
         if constexpr (DIM == 3) {
             if constexpr (MODE != 0) {
@@ -572,6 +573,7 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
             }
             if constexpr (MODE != 1) {
                 if (td.width == 16 && td.L == 8) EAMC_CK(8, 16);
+                else if (td.width == 8 && td.L == 8) EAMC_CK(8, 8);
                 else if (td.width == 8 && td.L == 10) EAMC_CK(10, 8);
                 else if (td.width == 4 && td.L == 12) EAMC_CK(12, 4);
             }
@@ -641,7 +643,7 @@ size_t checker_smem_bytes(int dim, int L, int width) {
     if (width != 32) {
         if (dim != 3) return 0;
         if (width == 16) return L == 7 ? CkGeo<3, 7, 16>::SMEM : (L == 8 ? CkGeo<3, 8, 16>::SMEM : 0);
-        if (width == 8) return L == 9 ? CkGeo<3, 9, 8>::SMEM : (L == 10 ? CkGeo<3, 10, 8>::SMEM : 0);
+        if (width == 8) return L == 8 ? CkGeo<3, 8, 8>::SMEM : (L == 9 ? CkGeo<3, 9, 8>::SMEM : (L == 10 ? CkGeo<3, 10, 8>::SMEM : 0));
         if (width == 4) return L == 11 ? CkGeo<3, 11, 4>::SMEM : (L == 12 ? CkGeo<3, 12, 4>::SMEM : 0);
         return 0;
     }
@@ -652,7 +654,7 @@ size_t checker_smem_bytes(int dim, int L, int width) {
 bool checker_thresholds_in_smem(int dim, int L, int width) {
     if (checker_smem_bytes(dim, L, width) == 0) return false;
 #define EAMC_TS(D, LL, WW) if (dim == D && L == LL && width == WW) return CkGeo<D, LL, WW>::SMEM_THR;
-    EAMC_TS(3, 7, 16) EAMC_TS(3, 8, 16) EAMC_TS(3, 9, 8) EAMC_TS(3, 10, 8) EAMC_TS(3, 11, 4) EAMC_TS(3, 12, 4)
+    EAMC_TS(3, 7, 16) EAMC_TS(3, 8, 16) EAMC_TS(3, 8, 8) EAMC_TS(3, 9, 8) EAMC_TS(3, 10, 8) EAMC_TS(3, 11, 4) EAMC_TS(3, 12, 4)
     EAMC_TS(3, 3, 32) EAMC_TS(3, 4, 32) EAMC_TS(3, 5, 32) EAMC_TS(3, 6, 32) EAMC_TS(3, 7, 32) EAMC_TS(3, 8, 32)
     EAMC_TS(3, 9, 32) EAMC_TS(3, 10, 32) EAMC_TS(3, 11, 32) EAMC_TS(3, 12, 32)
     EAMC_TS(2, 3, 32) EAMC_TS(2, 4, 32) EAMC_TS(2, 5, 32) EAMC_TS(2, 6, 32) EAMC_TS(2, 7, 32) EAMC_TS(2, 8, 32)

@@ -175,13 +175,16 @@ def tile_width_info(dim: int, L: int, width: int, order: int = 0):
     return smem.value, bool(in_smem.value)
 
 
+def narrow_widths(dim: int, L: int, order: int = 0) -> list:
+    """The tile widths below 32 available at (dim, L) in sweep order `order`, narrowest first."""
+    return [w for w in (4, 8, 16) if tile_width_info(dim, L, w, order)]
+
+
 def narrow_width(dim: int, L: int, order: int = 0) -> int:
     """The narrowest tile width available at (dim, L) in sweep order `order` (32 when there is
     no narrow one)."""
-    for w in (4, 8, 16):
-        if tile_width_info(dim, L, w, order):
-            return w
-    return 32
+    ws = narrow_widths(dim, L, order)
+    return ws[0] if ws else 32
 
 
 def check(rc: int) -> int:

@@ -206,10 +206,10 @@ def test_colour_snapshot_resume_and_narrow_tiles(eamc, orc):
     resumed.check()
 
 
-@pytest.mark.parametrize("L,width,n,sweeps", [(7, 16, 21, 10), (8, 16, 35, 10), (9, 8, 13, 6), (10, 8, 9, 6),
-                                              (11, 4, 6, 6), (12, 4, 5, 6)])
+@pytest.mark.parametrize("L,width,n,sweeps", [(7, 16, 21, 10), (8, 16, 35, 10), (8, 8, 19, 10), (9, 8, 13, 6),
+                                              (10, 8, 9, 6), (11, 4, 6, 6), (12, 4, 5, 6)])
 def test_narrow_colour_tiles_bit_exact(eamc, orc, L, width, n, sweeps):
-    """Tiles of 16 (L = 7, 8), 8 (L = 9, 10) and 4 chains (L = 11, 12), each chain on 32 / width
+    """Tiles of 16 (L = 7, 8), 8 (L = 8, 9, 10) and 4 chains (L = 11, 12), each chain on 32 / width
     lanes with its thresholds in shared memory and the producers' rows dealt to the lane groups:
     the colour order's trajectories, a partly filled last tile."""
     info = eamc.tile_width_info(3, L, width, order=1)
