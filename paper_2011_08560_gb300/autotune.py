@@ -45,9 +45,13 @@ def signature(groups) -> str:
     return ";".join(f"{d}x{L}x{n}" for d, L, n in groups)
 
 
+# above this many width assignments the tuner searches in stages instead of trying them all
+MAX_WIDTH_COMBOS = 12
+
+
 def width_options(groups, order: int = 0):
-    """Tile-width assignments to try: every L at 32, and each L that has narrow widths at each of
-    them (all combinations; at most a few sizes have one, at most two)."""
+    """Tile-width assignments: every L at 32, and each L that has narrow widths at each of them
+    (all combinations; tune() searches in stages when there are more than MAX_WIDTH_COMBOS)."""
     narrow = sorted({(d, L) for d, L, _ in groups if eamc.narrow_widths(d, L, order)})
     choices = [[32] + eamc.narrow_widths(d, L, order) for d, L in narrow]
     out = []
@@ -82,7 +86,8 @@ def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, dev
         return db[key]["best"]
     stream = torch.cuda.Stream(device=device)
     results = []
-    for widths in width_options(groups, order):
+
+    def trial(widths):
         ctx = eamc.Context(seed=0x5EED, device=device, stream=stream.cuda_stream)
         ctx.set_sweep_order(order)
         for L, w in widths.items():
@@ -105,6 +110,25 @@ def tune(groups, sweeps: int = 40, repeats: int = 2, use_cache: bool = True, dev
                 best = ms if best is None else min(best, ms)
             results.append({"widths": widths, **cand, "ms": best})
         ctx.close()
+        return min(r["ms"] for r in results if r["widths"] == widths)
+
+    combos = width_options(groups, order)
+    if len(combos) <= MAX_WIDTH_COMBOS:
+        for widths in combos:
+            trial(widths)
+    else:
+        # staged: every size's narrow widths alone (the others in full tiles), then the sizes'
+        # winners together
+        base = trial({})
+        pick = {}
+        for d, L in sorted({(d, L) for d, L, _ in groups if eamc.narrow_widths(d, L, order)}):
+            best_ms = base
+            for w in eamc.narrow_widths(d, L, order):
+                ms = trial({str(L): w})
+                if ms < best_ms:
+                    best_ms, pick[str(L)] = ms, w
+        if len(pick) > 1:
+            trial(dict(pick))
     winner = min(results, key=lambda r: r["ms"])
     best = {k: winner[k] for k in ("widths", "persistent", "blocks_per_sm", "sweeps_per_launch")}
     if use_cache:

@@ -636,7 +636,8 @@ extern "C" int muca_set_eg(ea_ctx *ctx, int chain0, int n, const int32_t *e_g) {
 
 // The colour order runs in the checkerboard kernels (one lane per chain in the tiles of the
 // lexicographic kernel; three colour passes for odd L, a kernel of their own); the shared memory
-// for the context's tiles and which parities occur (bit 0 even, bit 1 odd L).
+// for the context's tiles and which kernel-form classes occur (bit 0 even, bit 1 odd L, bit 2 the
+// small even sizes' narrow tiles).
 static int colour_launch(ea_ctx *ctx, size_t *ck_smem_out, int *parities) {
     int optin = 0;
     EA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
@@ -644,7 +645,7 @@ static int colour_launch(ea_ctx *ctx, size_t *ck_smem_out, int *parities) {
     int par = 0;
     for (const TileDesc &td : ctx->tiles) {
         ck = std::max(ck, checker_smem_bytes(td.dim, td.L, td.width));
-        par |= 1 << (td.L & 1);
+        par |= checker_parity_class(td.dim, td.L, td.width);
     }
     if (ck > (size_t)optin) return fail(EA_EINVAL, "the colour-order sweep does not fit in shared memory");
     *ck_smem_out = ck;

@@ -110,6 +110,9 @@ int sweep_blocks_per_sm(int dim, size_t smem);
 // L = 7, 8, 8 at L = 9, 10, 4 at L = 11, 12 (0 bytes: not available)
 size_t checker_smem_bytes(int dim, int L, int width);
 bool checker_thresholds_in_smem(int dim, int L, int width);
+// the kernel-form class of a tile in the colour order: 1 even L, 2 odd L, 4 the narrow tiles of the
+// small even sizes (3D, L <= 6), which run in forms of their own
+int checker_parity_class(int dim, int L, int width);
 cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim, size_t smem, SlotState *d_slots,
                                   uint32_t *d_spins, const uint32_t *d_bonds, const uint32_t *d_thr,
                                   uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,

@@ -558,16 +558,19 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileDesc td = tiles[blockIdx.x];
     const bool odd = (td.L & 1) != 0;
-    if ((MODE == 0 && odd) || (MODE == 1 && !odd)) return;  // the whole CTA, before any barrier
+    if (((MODE == 0 || MODE == 3) && odd) || (MODE == 1 && !odd)) return;  // the whole CTA, before any barrier
     const uint64_t n_tile = n_sweeps * (uint64_t)(td.sweep_mul > 0 ? td.sweep_mul : 1);
 #define EAMC_CK(LL, WW) checker_tile<DIM, LL, WW>(td, blockIdx.x, slots, spins, bonds, thr, hist, n_tile, key, count_rt, diag, smem_raw)
-    // narrow tiles (3D): 16 chains at L = 7, 8, 8 at L = 8, 9, 10, 4 at L = 11, 12, each chain on
-    // 32 / width lanes, so that the thresholds fit in shared memory (at L = 8 tiles of 8 spread a
-    // batch over twice the SMs, each with half the producer work)
+    // narrow tiles (3D): 16 chains at L = 4..8, 8 at L = 4..10, 4 at L = 11, 12, each chain on
+    // 32 / width lanes, so that the thresholds fit in shared memory (L >= 7) or a batch spreads
+    // over more SMs, each with a smaller share of the producer work (L <= 8)
     if (td.width != 32) {
         if constexpr (DIM == 3) {
-            if constexpr (MODE != 0) {
+            if constexpr (MODE == 1 || MODE == 2) {
                 if (td.width == 16 && td.L == 7) EAMC_CK(7, 16);
+                else if (td.width == 8 && td.L == 7) EAMC_CK(7, 8);
+                else if (td.width == 16 && td.L == 5) EAMC_CK(5, 16);
+                else if (td.width == 8 && td.L == 5) EAMC_CK(5, 8);
                 else if (td.width == 8 && td.L == 9) EAMC_CK(9, 8);
                 else if (td.width == 4 && td.L == 11) EAMC_CK(11, 4);
             }
@@ -577,10 +580,18 @@ muca_checker_kernel(const TileDesc *__restrict__ tiles, SlotState *__restrict__ 
                 else if (td.width == 8 && td.L == 10) EAMC_CK(10, 8);
                 else if (td.width == 4 && td.L == 12) EAMC_CK(12, 4);
             }
+            // the small even sizes' narrow tiles in forms of their own (MODE 3, and 2 for both
+            // parities): compiled into the even-size form they cost L = 8 1 % through its code
+            if constexpr (MODE >= 2) {
+                if (td.width == 16 && td.L == 4) EAMC_CK(4, 16);
+                else if (td.width == 8 && td.L == 4) EAMC_CK(4, 8);
+                else if (td.width == 16 && td.L == 6) EAMC_CK(6, 16);
+                else if (td.width == 8 && td.L == 6) EAMC_CK(6, 8);
+            }
         }
         return;
     }
-    if constexpr (MODE != 0) {
+    if constexpr (MODE == 1 || MODE == 2) {
         switch (td.L) {
             case 3: EAMC_CK(3, 32); break;
             case 5: EAMC_CK(5, 32); break;
@@ -642,8 +653,28 @@ size_t checker_smem_bytes(int dim, int L, int width) {
     if (L < 3 || L > 12) return 0;
     if (width != 32) {
         if (dim != 3) return 0;
-        if (width == 16) return L == 7 ? CkGeo<3, 7, 16>::SMEM : (L == 8 ? CkGeo<3, 8, 16>::SMEM : 0);
-        if (width == 8) return L == 8 ? CkGeo<3, 8, 8>::SMEM : (L == 9 ? CkGeo<3, 9, 8>::SMEM : (L == 10 ? CkGeo<3, 10, 8>::SMEM : 0));
+        if (width == 16) {
+            switch (L) {
+                case 4: return CkGeo<3, 4, 16>::SMEM;
+                case 5: return CkGeo<3, 5, 16>::SMEM;
+                case 6: return CkGeo<3, 6, 16>::SMEM;
+                case 7: return CkGeo<3, 7, 16>::SMEM;
+                case 8: return CkGeo<3, 8, 16>::SMEM;
+                default: return 0;
+            }
+        }
+        if (width == 8) {
+            switch (L) {
+                case 4: return CkGeo<3, 4, 8>::SMEM;
+                case 5: return CkGeo<3, 5, 8>::SMEM;
+                case 6: return CkGeo<3, 6, 8>::SMEM;
+                case 7: return CkGeo<3, 7, 8>::SMEM;
+                case 8: return CkGeo<3, 8, 8>::SMEM;
+                case 9: return CkGeo<3, 9, 8>::SMEM;
+                case 10: return CkGeo<3, 10, 8>::SMEM;
+                default: return 0;
+            }
+        }
         if (width == 4) return L == 11 ? CkGeo<3, 11, 4>::SMEM : (L == 12 ? CkGeo<3, 12, 4>::SMEM : 0);
         return 0;
     }
@@ -651,10 +682,16 @@ size_t checker_smem_bytes(int dim, int L, int width) {
     return dim == 3 ? checker_smem_w<3, 32>(L) : checker_smem_w<2, 32>(L);
 }
 
+int checker_parity_class(int dim, int L, int width) {
+    if (L & 1) return 2;
+    return (dim == 3 && width != 32 && L <= 6) ? 4 : 1;
+}
+
 bool checker_thresholds_in_smem(int dim, int L, int width) {
     if (checker_smem_bytes(dim, L, width) == 0) return false;
 #define EAMC_TS(D, LL, WW) if (dim == D && L == LL && width == WW) return CkGeo<D, LL, WW>::SMEM_THR;
-    EAMC_TS(3, 7, 16) EAMC_TS(3, 8, 16) EAMC_TS(3, 8, 8) EAMC_TS(3, 9, 8) EAMC_TS(3, 10, 8) EAMC_TS(3, 11, 4) EAMC_TS(3, 12, 4)
+    EAMC_TS(3, 7, 16) EAMC_TS(3, 8, 16) EAMC_TS(3, 8, 8) EAMC_TS(3, 4, 16) EAMC_TS(3, 5, 16) EAMC_TS(3, 6, 16)
+    EAMC_TS(3, 4, 8) EAMC_TS(3, 5, 8) EAMC_TS(3, 6, 8) EAMC_TS(3, 7, 8) EAMC_TS(3, 9, 8) EAMC_TS(3, 10, 8) EAMC_TS(3, 11, 4) EAMC_TS(3, 12, 4)
     EAMC_TS(3, 3, 32) EAMC_TS(3, 4, 32) EAMC_TS(3, 5, 32) EAMC_TS(3, 6, 32) EAMC_TS(3, 7, 32) EAMC_TS(3, 8, 32)
     EAMC_TS(3, 9, 32) EAMC_TS(3, 10, 32) EAMC_TS(3, 11, 32) EAMC_TS(3, 12, 32)
     EAMC_TS(2, 3, 32) EAMC_TS(2, 4, 32) EAMC_TS(2, 5, 32) EAMC_TS(2, 6, 32) EAMC_TS(2, 7, 32) EAMC_TS(2, 8, 32)
@@ -668,9 +705,18 @@ cudaError_t launch_sweeps_checker(const TileDesc *d_tiles, int n_tiles, int dim,
                                   uint32_t *d_hist, uint64_t n_sweeps, PhiloxKey key, int count_rt,
                                   unsigned *d_diag, cudaStream_t st, int parities) {
     if (n_tiles <= 0 || n_sweeps == 0 || parities == 0) return cudaSuccess;
-    const int mode = parities == 1 ? 0 : (parities == 2 ? 1 : 2);
+    // bit 0 even sizes, bit 1 odd sizes, bit 2 the small even sizes' narrow tiles
+    const bool odd = (parities & 2) != 0, small = (parities & 4) != 0;
+    const int mode = odd ? ((parities & 5) ? 2 : 1) : (small ? 3 : 0);
 #define EAMC_CKL(D, M) ck_launch<D, M>(n_tiles, smem, st, d_tiles, d_slots, d_spins, d_bonds, d_thr, d_hist, n_sweeps, key, count_rt, d_diag)
-    if (dim == 3) return mode == 0 ? EAMC_CKL(3, 0) : (mode == 1 ? EAMC_CKL(3, 1) : EAMC_CKL(3, 2));
+    if (dim == 3) {
+        switch (mode) {
+            case 0: return EAMC_CKL(3, 0);
+            case 1: return EAMC_CKL(3, 1);
+            case 3: return EAMC_CKL(3, 3);
+            default: return EAMC_CKL(3, 2);
+        }
+    }
     return mode == 0 ? EAMC_CKL(2, 0) : (mode == 1 ? EAMC_CKL(2, 1) : EAMC_CKL(2, 2));
 #undef EAMC_CKL
 }

@@ -48,13 +48,16 @@ def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
 
 def test_tile_width_options_per_order():
     """Host-side width queries (no GPU): the lexicographic kernel has tiles of 16 at L = 7, 8; the
-    colour-order kernel has 16 at L = 7, 8, 8 at L = 8, 9, 10 and 4 at L = 11, 12 (3D), and the
-    autotuner tries every one of them beside full tiles."""
+    colour-order kernel has 16 at L = 4..8, 8 at L = 4..10 and 4 at L = 11, 12 (3D), and the
+    autotuner tries every one of them beside full tiles (in stages when the combinations are
+    many)."""
     from paper_2011_08560_gb300 import autotune, build, eamc
     build.build()
     assert eamc.narrow_widths(3, 8, 0) == [16] and eamc.narrow_widths(3, 8, 1) == [8, 16]
-    assert eamc.narrow_widths(3, 6, 1) == [] and eamc.narrow_widths(2, 8, 1) == []
-    assert [eamc.narrow_width(3, L, 1) for L in range(4, 13)] == [32, 32, 32, 16, 8, 8, 8, 4, 4]
+    assert eamc.narrow_widths(3, 6, 0) == [] and eamc.narrow_widths(3, 6, 1) == [8, 16]
+    assert eamc.narrow_widths(2, 8, 1) == [] and eamc.narrow_widths(3, 3, 1) == []
+    assert [eamc.narrow_width(3, L, 1) for L in range(4, 13)] == [8, 8, 8, 8, 8, 8, 8, 4, 4]
     assert autotune.width_options([(3, 8, 1024)], 0) == [{}, {"8": 16}]
     assert autotune.width_options([(3, 8, 1024)], 1) == [{}, {"8": 8}, {"8": 16}]
-    assert len(autotune.width_options([(3, L, 10) for L in (4, 6, 8, 10, 12)], 1)) == 3 * 2 * 2
+    assert len(autotune.width_options([(3, L, 10) for L in (4, 6, 8, 10, 12)], 1)) == 3 * 3 * 3 * 2 * 2
+    assert len(autotune.width_options([(3, L, 10) for L in (4, 6, 8, 10, 12)], 0)) == 2

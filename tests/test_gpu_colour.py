@@ -206,16 +206,18 @@ def test_colour_snapshot_resume_and_narrow_tiles(eamc, orc):
     resumed.check()
 
 
-@pytest.mark.parametrize("L,width,n,sweeps", [(7, 16, 21, 10), (8, 16, 35, 10), (8, 8, 19, 10), (9, 8, 13, 6),
+@pytest.mark.parametrize("L,width,n,sweeps", [(4, 16, 37, 40), (4, 8, 13, 40), (5, 16, 20, 30), (5, 8, 11, 30),
+                                              (6, 16, 18, 20), (6, 8, 21, 20), (7, 16, 21, 10), (7, 8, 9, 10),
+                                              (8, 16, 35, 10), (8, 8, 19, 10), (9, 8, 13, 6),
                                               (10, 8, 9, 6), (11, 4, 6, 6), (12, 4, 5, 6)])
 def test_narrow_colour_tiles_bit_exact(eamc, orc, L, width, n, sweeps):
-    """Tiles of 16 (L = 7, 8), 8 (L = 8, 9, 10) and 4 chains (L = 11, 12), each chain on 32 / width
+    """Tiles of 16 (L = 4..8), 8 (L = 4..10) and 4 chains (L = 11, 12), each chain on 32 / width
     lanes with its thresholds in shared memory and the producers' rows dealt to the lane groups:
     the colour order's trajectories, a partly filled last tile."""
     info = eamc.tile_width_info(3, L, width, order=1)
     assert info is not None and info[1], info           # thresholds in shared memory
     lex_has_width = eamc.tile_width_info(3, L, width, order=0) is not None
-    assert lex_has_width == (width == 16)
+    assert lex_has_width == (width == 16 and L in (7, 8))
     rng = np.random.default_rng(L * 7 + width)
     ctx = eamc.Context(seed=SEED)
     ctx.set_sweep_order(eamc.EA_ORDER_COLOUR)
@@ -237,3 +239,26 @@ def test_narrow_colour_tiles_bit_exact(eamc, orc, L, width, n, sweeps):
         ctx.set_sweep_order(eamc.EA_ORDER_LEX)
         with pytest.raises(eamc.EamcError):
             ctx.run_sweeps(1)
+
+
+@pytest.mark.parametrize("shapes", [((4, 8, 11), (6, 16, 18), (8, 8, 10)), ((5, 8, 9), (6, 8, 12), (8, 16, 7))])
+def test_small_narrow_tiles_in_mixed_contexts(eamc, orc, shapes):
+    """Narrow tiles of the small even sizes beside other sizes in one context: with even sizes
+    only they run in a kernel form of their own, with an odd size in the form for both parities;
+    every chain's trajectory is the oracle's."""
+    rng = np.random.default_rng(sum(L * w for L, w, _ in shapes))
+    ctx = eamc.Context(seed=SEED)
+    ctx.set_sweep_order(eamc.EA_ORDER_COLOUR)
+    chains, rid = [], 31
+    for L, w, n in shapes:
+        ctx.set_tile_width(L, w)
+        ctx.init_disorder(3, L, n, rid0=rid, stream=2)
+        chains += _chains(orc, 3, L, n, rid, 2)
+        rid += n
+    thr = [orc.quantize(3, _random_lnw(rng, c.b_top, 0.4)) for c in chains]
+    ctx.set_thresholds(0, _pad(thr))
+    ctx.run_sweeps(12, count_roundtrips=True)
+    for c, th in zip(chains, thr):
+        c.sweeps(12, th, count_rt=True)
+    _compare(ctx, chains)
+    ctx.check()

@@ -182,7 +182,7 @@ def test_mixed_widths_in_one_context(eamc, orc, persistent):
 
 def test_tile_width_rejects_unavailable(eamc):
     ctx = eamc.Context(seed=SEED)
-    for L, w in ((6, 16), (12, 16), (6, 8), (8, 4), (8, 64)):
+    for L, w in ((12, 16), (6, 4), (3, 8), (8, 4), (8, 64)):
         with pytest.raises(eamc.EamcError):
             ctx.set_tile_width(L, w)
     assert eamc.tile_width_info(3, 6, 16) is None
