@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--only", choices=["pt", "pt_protocol", "uneven", "serving", "serving_saturated",
                                        "recursion", "scan", "small", "flat", "l6", "table_one_l8",
                                        "paper_samples", "lex", "uneven_checkerboard",
-                                       "table_one_l8_checkerboard", "scan_checkerboard", "serving_colour"],
+                                       "table_one_l8_checkerboard", "scan_checkerboard", "serving_colour",
+                                       "serving_lex"],
                     default=None,
                     help="run one secondary workload alone and print its record (profiling)")
     ap.add_argument("--no-tune", action="store_true",
@@ -1051,7 +1052,8 @@ def main():
     if args.only:
         fn = {"pt": lambda: bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol,
               "uneven": bench_uneven, "uneven_checkerboard": lambda: bench_uneven(order=1),
-              "serving": bench_serving, "serving_colour": lambda: bench_serving(order=1),
+              "serving": lambda: bench_serving(order=1), "serving_colour": lambda: bench_serving(order=1),
+              "serving_lex": lambda: bench_serving(order=0),
               "scan": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps),
               "scan_checkerboard": lambda: bench_profile_scan(L=args.scan_L, prod_sweeps=args.scan_prod_sweeps,
                                                               order=1),
@@ -1076,7 +1078,8 @@ def main():
                   "table_one_l8_checkerboard": bench_table_one_l8(order=1),
                   "l6_flat_pl": bench_l6_flat_pl(),
                   "small": bench_small(), "pt": bench_pt(args.pt_sweeps), "pt_protocol": bench_pt_protocol(),
-                  "uneven": bench_uneven(), "serving": bench_serving(),
+                  "uneven": bench_uneven(), "serving": bench_serving(order=1),
+                  "serving_lexicographic": bench_serving(order=0),
                   "serving_saturated": bench_serving_saturated(), "recursion": bench_recursion(),
                   "scan": bench_profile_scan(), "scan_checkerboard": bench_profile_scan(order=1)}
     if rank != 0:
