@@ -121,7 +121,11 @@ struct CkGeo {
     static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * W * 16;
     static constexpr size_t RES_BYTES = (size_t)2 * NA * W * sizeof(int);  // bin row offset after each attempt, two records
     static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * W * sizeof(uint32_t);
-    static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES;
+    // odd L: each (pass, row)'s colour sites as nibble positions, padding slots at 0 (rows of a
+    // pass padded to whole records)
+    static constexpr int NPR = NP * RPR;
+    static constexpr size_t FSH_BYTES = (L & 1) ? ((size_t)NCOL * NPR * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES + FSH_BYTES;
     static constexpr bool SMEM_THR = BASE_BYTES + THR_BYTES <= 225 * 1024;
     static constexpr size_t SMEM = BASE_BYTES + (SMEM_THR ? THR_BYTES : 0);
     // thresholds addressed by 32-bit shared addresses; measured with the same launches: L = 6 in
@@ -166,6 +170,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     T *JBs = Rs + NR * W;
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
     int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2 records][NA][W]
+    uint32_t *ftab = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES + G::RES_BYTES);
     // odd L: for each colour shift s, the row's colour sites as a byte list (x positions, 0xFF
     // for padding slots) and their number
     __shared__ uint32_t s_xs[3];
@@ -192,6 +197,19 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
         if constexpr (ODD) return ((c - ck_ax(L, y) - (DIM == 3 ? ck_ax(L, z) : 0)) % 3 + 3) % 3;
         else return (c + y + z) & 1;
     };
+    if constexpr (ODD) {  // the consumer's per-row flip positions, once per launch
+        for (int e = threadIdx.x; e < NCOL * G::NPR; e += blockDim.x) {
+            const int c = e / G::NPR, r = e % G::NPR;
+            uint32_t v = 0u;
+            if (r < NR) {
+                const int sh = row_shift(c, r);
+                int n = 0;
+                for (int x = 0; x < L; ++x)
+                    if (ck_ax(L, x) == sh) { v |= (uint32_t)x << (8 * n); ++n; }
+            }
+            ftab[e] = v;  // unused slots: position 0 (they never accept)
+        }
+    }
     const uint32_t *gsp = spins + td.spin_off;
     const uint32_t *gbd = bonds + td.bond_off;
     for (int row = warp; row < NR; row += kCkWarps) {
@@ -473,10 +491,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
             for (int h = 0; h < RPR; ++h) {
                 flipped[h] = 0;
                 rold[h] = (!PADROWS || r0 + h < NR) ? Rs[(r0 + h) * W + ln] : T(0);
-                if constexpr (ODD) {  // padding bytes (0xFF) become x = 0: they never accept
-                    const uint32_t xs = r0 + h < NR ? s_xs[row_shift(c, r0 + h)] : 0u;
-                    fsh[h] = xs & ~(((xs >> 7) & 0x01010101u) * 0xFFu);
-                }
+                if constexpr (ODD) fsh[h] = ftab[c * G::NPR + r0 + h];  // padding slots at x = 0: they never accept
             }
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
