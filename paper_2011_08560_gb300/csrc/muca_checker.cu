@@ -121,10 +121,10 @@ struct CkGeo {
     static constexpr size_t HAND_BYTES = (size_t)NBUF * HQ * W * 16;
     static constexpr size_t RES_BYTES = (size_t)2 * NA * W * sizeof(int);  // bin row offset after each attempt, two records
     static constexpr size_t THR_BYTES = (size_t)(B + 2 * DIM) * 8 * W * sizeof(uint32_t);
-    // odd L: each (pass, row)'s colour sites as nibble positions, padding slots at 0 (rows of a
-    // pass padded to whole records)
+    // odd L: each (pass, row)'s colour sites as nibble positions, padding slots at 0 for the
+    // consumer and 0xFF for the producers (two tables; rows of a pass padded to whole records)
     static constexpr int NPR = NP * RPR;
-    static constexpr size_t FSH_BYTES = (L & 1) ? ((size_t)NCOL * NPR * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t FSH_BYTES = (L & 1) ? ((size_t)2 * NCOL * NPR * 4 + 15) / 16 * 16 : 0;
     static constexpr size_t BASE_BYTES = LATTICE_BYTES + HAND_BYTES + RES_BYTES + FSH_BYTES;
     static constexpr bool SMEM_THR = BASE_BYTES + THR_BYTES <= 225 * 1024;
     static constexpr size_t SMEM = BASE_BYTES + (SMEM_THR ? THR_BYTES : 0);
@@ -171,27 +171,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     uint4 *hand = reinterpret_cast<uint4 *>(smem_raw + G::LATTICE_BYTES);
     int *res = reinterpret_cast<int *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES);  // [2 records][NA][W]
     uint32_t *ftab = reinterpret_cast<uint32_t *>(smem_raw + G::LATTICE_BYTES + G::HAND_BYTES + G::RES_BYTES);
-    // odd L: for each colour shift s, the row's colour sites as a byte list (x positions, 0xFF
-    // for padding slots) and their number
-    __shared__ uint32_t s_xs[3];
-    __shared__ int s_ns[3];
-    if constexpr (ODD) {
-        if (threadIdx.x < 3) {
-            const int sh = threadIdx.x;
-            uint32_t pk = 0xFFFFFFFFu;
-            int n = 0;
-            for (int x = 0; x < L; ++x) {
-                if (ck_ax(L, x) == sh) {
-                    pk = (pk & ~(0xFFu << (8 * n))) | ((uint32_t)x << (8 * n));
-                    ++n;
-                }
-            }
-            s_xs[sh] = pk;
-            s_ns[sh] = n;
-        }
-    }
     // the colour shift of row r in pass c: its colour sites are x0 + 2j (even L, x0 = the shift)
-    // or the list of shift s (odd L)
+    // or the x with ax(x) = s (odd L)
     auto row_shift = [](int c, int r) -> int {
         const int y = r % L, z = DIM == 3 ? r / L : 0;
         if constexpr (ODD) return ((c - ck_ax(L, y) - (DIM == 3 ? ck_ax(L, z) : 0)) % 3 + 3) % 3;
@@ -200,14 +181,19 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
     if constexpr (ODD) {  // the consumer's per-row flip positions, once per launch
         for (int e = threadIdx.x; e < NCOL * G::NPR; e += blockDim.x) {
             const int c = e / G::NPR, r = e % G::NPR;
-            uint32_t v = 0u;
+            uint32_t v = 0u, raw = 0xFFFFFFFFu;
             if (r < NR) {
                 const int sh = row_shift(c, r);
                 int n = 0;
                 for (int x = 0; x < L; ++x)
-                    if (ck_ax(L, x) == sh) { v |= (uint32_t)x << (8 * n); ++n; }
+                    if (ck_ax(L, x) == sh) {
+                        v |= (uint32_t)x << (8 * n);
+                        raw = (raw & ~(0xFFu << (8 * n))) | ((uint32_t)x << (8 * n));
+                        ++n;
+                    }
             }
             ftab[e] = v;  // unused slots: position 0 (they never accept)
+            ftab[NCOL * G::NPR + e] = raw;
         }
     }
     const uint32_t *gsp = spins + td.spin_off;
@@ -295,7 +281,8 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                             buf[(G::OFFQ + h * NGC + g) * W + ln] = w;
                         }
                     } else {
-                        const int nreal = r >= NR ? 0 : (ODD ? s_ns[row_shift(c, r)] : HALF);
+                        // odd L: the row's sites, the bytes of its list that are not 0xFF
+                        const int nreal = r >= NR ? 0 : (ODD ? 4 - __popc((ftab[(NCOL + c) * G::NPR + r] >> 7) & 0x01010101u) : HALF);
 #pragma unroll
                         for (int g = 0; g < NGC; ++g) {
                             uint4 w = make_uint4(kAlways, kAlways, kAlways, kAlways);
@@ -347,7 +334,7 @@ __device__ __forceinline__ void checker_tile(const TileDesc &td, int tile, SlotS
                 }
                 if constexpr (ODD) {
                     s = sum;
-                    xs = s_xs[row_shift(c, r)];
+                    xs = ftab[(NCOL + c) * G::NPR + r];
                 } else {
                     s = sum >> (4 * row_shift(c, r));  // nibble 2j: the j-th colour site
                 }
