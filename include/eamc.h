@@ -169,13 +169,14 @@ int muca_set_sweep_order(ea_ctx *ctx, int order, int chains_per_cta);
 
 /* a8 -- chains per tile for chains of linear size L added afterwards (ea_init_disorder):
  * width 32 (the default, every L), 16 (3D, L = 7, 8), or, for chains swept in the colour order
- * only, 8 (3D, L = 8, 9, 10) and 4 (3D, L = 11, 12); muca_run_sweeps in the lexicographic order
- * refuses tiles of those two widths (EA_EINVAL).  A tile is one
+ * only, 16 (3D, L = 4, 5, 6), 8 (3D, L = 4..10) and 4 (3D, L = 11, 12); muca_run_sweeps in the
+ * lexicographic order refuses tiles of a width that kernel lacks (EA_EINVAL).  A tile is one
  * warp; with width W < 32 each of its W chains runs on 32/W lanes side by side, so the tile needs
- * W/32 of the shared memory of a full one and these sizes keep their acceptance thresholds in
- * shared memory instead of reading them through L1: each chain runs faster, the SM holds fewer
- * chains.  Narrow tiles suit batches with fewer chains than the GPU can hold; results do not
- * depend on the width.  EA_EINVAL for a width not available at this L. */
+ * W/32 of the shared memory of a full one: at L >= 7 the acceptance thresholds then fit in shared
+ * memory instead of being read through L1, and at every L a batch spreads over more SMs with less
+ * producer work on each; each chain runs faster, the SM holds fewer chains.  Narrow tiles suit
+ * batches with fewer chains than the GPU can hold; results do not depend on the width.
+ * EA_EINVAL for a width not available at this L. */
 int muca_set_tile_width(ea_ctx *ctx, int L, int width);
 
 /* Properties of the sweep kernel for tiles of (dim, L, width): dynamic shared memory per block
