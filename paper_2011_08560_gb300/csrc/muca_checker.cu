@@ -1,9 +1,10 @@
 // muca_checker.cu -- a2 + a3 in the colour order (the checkerboard for even L): the
 // multicanonical sweep (Sec. II, Eq. "muca") with the sites of a sweep taken colour by colour,
-// each colour in lexicographic order, for 32 (or 16) independent chains per tile, one lane per
-// chain.  Odd L (three colours, the PT colouring) runs in the same kernel: a row has a varying
-// number of sites of a colour, so each row gets the largest number of attempt slots and the
-// unused ones are padding that moves nothing and never accepts.
+// each colour in lexicographic order, for 32, 16, 8 or 4 independent chains per tile, one lane
+// per chain (a narrow tile's chains on 32 / width lanes each).  Odd L (three colours, the PT
+// colouring) runs in the same kernel: a row has a varying number of sites of a colour, so each
+// row gets the largest number of attempt slots and the unused ones are padding that moves
+// nothing and never accepts; each (pass, row)'s sites come from tables made once per launch.
 //
 // In a colour pass no two attempted sites are neighbours, so the class n of every attempt
 // (unsatisfied bonds, the move changes the bin by dim - n) is fixed when the pass begins.  The
@@ -19,8 +20,8 @@
 // of these warps as well); 2 the measurement (lowest energy, round trips, histogram), one record
 // behind the consumer; 4 and 7 only take part in the barriers.  A record is RPR consecutive rows
 // of one pass (two to eight, by size): the colour-c sites of those rows, RPR L / 2 attempts for
-// even L, with each attempt's class as its table offset n * NSB (16 bits) and its random word.  The consumer leaves the bin after every attempt for the
-// measurement.  Within a pass the producers may run any number of records ahead (the classes
+// even L, with each attempt's class as its table offset n * NSB (16 bits) and its random word.
+// The consumer leaves the bin after every attempt for the measurement.  Within a pass the producers may run any number of records ahead (the classes
 // read only the other colour's spins and each site's own spin, which its own record changes), so
 // they run LAG records ahead; at the start of a pass one extra barrier lets them refill, because
 // the first plane's classes read the last plane of the previous pass.
@@ -28,9 +29,9 @@
 // Random words (the colour-order streams): the j-th colour-c site of row r takes word j&3 of
 // Philox call (4 r + j/4, t, rid, (5 + c) | stream << 8).
 //
-// Lattice layout as in the lexicographic kernel: row words with one nibble per site (bit 0
-// used), chain-interleaved; thresholds lane-interleaved in shared memory when they fit, else
-// read through L1.
+// Lattice layout: row words with one nibble per site, chain-interleaved: the spins (bit 0) and
+// the bonds (Jx, Jy, Jz at bits 0, 1, 2); thresholds lane-interleaved in shared memory when they
+// fit, else read through L1.
 #include <cuda_runtime.h>
 
 #include <cstdint>
